@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark: effective bop/s (2mkn/t) of the GF(2) and Boolean bit-matrix
+products on square seeded Bernoulli inputs, through the C ABI.
+
+One step = one GF(2) product (through the alternative-basis Strassen
+recursion, depth chosen by the planner) plus one Boolean product (cubic), both
+at m = k = n = 32768 by default. Inputs are resident in HBM before the timed
+region; the step touches ~1.7 GB (> L2), so no L2 flush is needed between
+steps. `value` counts 2*m*k*n bit operations per product.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU
+(independent replicas, weak scaling); rank 0 prints one JSON line.
+--impl reference times the CPU oracle on a bounded row sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "effective bop/s (2mkn/t) Boolean & GF(2) products, tensor-core vs popcount path"
+
+# name: (n, seed, Boolean density); GF(2) operands are dense (p = 1/2).
+WORKLOADS = {
+    "square32768": (32768, 2, "2^-7.5"),
+    "square4096": (4096, 1, "1/64"),
+    "square65536": (65536, 3, "2^-8"),
+}
+DEFAULT_WORKLOAD = "square32768"
+# Matrix ids of the generator streams: GF(2) pair (0, 1), Boolean pair (4, 5).
+IDS_GF2 = (0, 1)
+IDS_BOOL = (4, 5)
+
+# 32-bit LOP3 results per SM per clock on sm_103 (measured).
+LOP3_LANES_PER_SM_CLK = 64
+# Nominal dense FP8 : BF16 tensor throughput ratio (4.5 : 2.25 PFLOP/s).
+FP8_PER_BF16 = 2.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--path", choices=["auto", "fp8", "i8", "popc"], default="auto")
+    ap.add_argument("--depth", type=int, default=-1, help="Strassen depth of the GF(2) product")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(n: int, seed: int, bool_p: str, rows: int):
+    """Time the oracle on rows 0..rows-1 of both products (inputs generated
+    outside the timed region). Returns (seconds, bit operations, threads)."""
+    import bitgen
+    import oracle
+
+    Bg = bitgen.fill_cpu(n, n, seed, IDS_GF2[1])
+    Bb = bitgen.fill_cpu(n, n, seed, IDS_BOOL[1], p=bool_p)
+    Ag = bitgen.fill_cpu(n, n, seed, IDS_GF2[0], row0=0, nrows=rows)
+    Ab = bitgen.fill_cpu(n, n, seed, IDS_BOOL[0], p=bool_p, row0=0, nrows=rows)
+    th = oracle.threads()
+    t0 = time.perf_counter()
+    oracle.rows(oracle.GF2, Ag, Bg, n, n, th)
+    oracle.rows(oracle.BOOL, Ab, Bb, n, n, th)
+    dt = time.perf_counter() - t0
+    return dt, 2 * (2 * rows * n * n), th
+
+
+def calibrated_rows(n: int, seed: int, bool_p: str, target_s: float) -> int:
+    r = 32
+    dt, _, _ = oracle_sample(n, seed, bool_p, r)
+    want = int(r * target_s / max(dt, 1e-3))
+    want = max(32, min(n, want // 32 * 32))
+    return want
+
+
+def cpu_baseline(n: int, seed: int, bool_p: str) -> dict:
+    rows = calibrated_rows(n, seed, bool_p, 12.0)
+    dt, bops, th = oracle_sample(n, seed, bool_p, rows)
+    return {"value": bops / dt, "unit": "bop/s", "cores": th, "kind": "oracle",
+            "sample": f"rows 0..{rows - 1} of the GF(2) and the Boolean product at "
+                      f"m=k=n={n} ({rows} of {n} rows, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n, seed, bool_p = WORKLOADS[args.workload]
+    rows = calibrated_rows(n, seed, bool_p, 3.0)
+    for _ in range(args.warmup):
+        oracle_sample(n, seed, bool_p, rows)
+    tot_s, tot_b, th = 0.0, 0, 1
+    for _ in range(args.steps):
+        dt, b, th = oracle_sample(n, seed, bool_p, rows)
+        tot_s += dt
+        tot_b += b
+    value = tot_b / tot_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "bop/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded SplitMix64 Bernoulli bits)",
+        "config": {"workload": args.workload, "m": n, "k": n, "n": n,
+                   "sample_rows_per_step": rows},
+        "cpu_baseline": {"value": value, "unit": "bop/s", "cores": th, "kind": "oracle",
+                         "sample": f"rows 0..{rows - 1} of both products per step"},
+        "e2e": {"value": value, "unit": "bop/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import bitgen
+    import paper_1909_01554_gb300 as bmm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    n, seed, bool_p = WORKLOADS[args.workload]
+    m = k = n
+    path = {"auto": bmm.PATH_AUTO, "fp8": bmm.PATH_TC_FP8, "i8": bmm.PATH_TC_I8,
+            "popc": bmm.PATH_POPC}[args.path]
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    # inputs resident in HBM (device generator; same stream definition as the CPU one)
+    def gen(rows, cols, mid, p):
+        t = bmm.empty(rows, cols)
+        bitgen.fill_device(t, cols, seed, mid, p=p, stream=sh)
+        return t
+
+    Ag, Bg = gen(m, k, IDS_GF2[0], None), gen(k, n, IDS_GF2[1], None)
+    Ab, Bb = gen(m, k, IDS_BOOL[0], bool_p), gen(k, n, IDS_BOOL[1], bool_p)
+    Cg, Cb = bmm.empty(m, n), bmm.empty(m, n)
+    kw_g = {"path": path, "depth": args.depth}
+    kw_b = {"path": path, "depth": 0}
+
+    def step(A1, B1, C1, A2, B2, C2):
+        bmm.gf2(A1, B1, C1, m, k, n, stream=sh, **kw_g)
+        bmm.boolean(A2, B2, C2, m, k, n, stream=sh, **kw_b)
+
+    for _ in range(args.warmup):
+        step(Ag, Bg, Cg, Ab, Bb, Cb)
+    bmm.stream_status(sh)
+    torch.cuda.synchronize()
+    barrier()
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    bmm.trace_enable(True)
+    l0 = bmm.launch_count()
+    sampler.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(Ag, Bg, Cg, Ab, Bb, Cb)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = bmm.launch_count() - l0
+    bmm.trace_enable(False)
+    bmm.stream_status(sh)
+    ms = ev0.elapsed_time(ev1)
+    base_n, base_ms = bmm.trace_read(bmm.PHASE_BASE)
+    xor_n, xor_ms = bmm.trace_read(bmm.PHASE_XOR)
+    tr_n, tr_ms = bmm.trace_read(bmm.PHASE_TRANSPOSE)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    bops_step = 2 * (2 * m * k * n)
+    value = world * bops_step * args.steps / (ms / 1000.0)
+
+    # plan facts for the roofline of the base case (the dominant kernel)
+    pg = bmm.plan(bmm.GF2, m, k, n, **kw_g)
+    pb = bmm.plan(bmm.BOOL, m, k, n, **kw_b)
+    depth_g, leaves = pg["strassen_depth"], pg["leaves"]
+    lm, lk, ln = m >> depth_g, k >> depth_g, n >> depth_g
+    flops_base_step = 2 * leaves * lm * lk * ln + 2 * m * k * n  # GF(2) leaves + Boolean
+    resolved = pg["path"]
+    pk, pk_kind = peaks()
+    if resolved in (bmm.PATH_TC_FP8, bmm.PATH_TC_I8):
+        peak = pk["bf16_tflops_sustained"] * FP8_PER_BF16
+        achieved = flops_base_step * args.steps / (base_ms / 1000.0) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{pk_kind} bf16 sustained x {FP8_PER_BF16} (nominal fp8:bf16)"}
+        dtype = "e4m3" if resolved == bmm.PATH_TC_FP8 else "u8"
+    else:
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak = sms * LOP3_LANES_PER_SM_CLK * pk["sm_max_mhz"] * 1e6 * 64 / 1e12
+        achieved = flops_base_step * args.steps / (base_ms / 1000.0) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tbop/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{sms} SMs x {LOP3_LANES_PER_SM_CLK} LOP3/clk x "
+                               f"{pk['sm_max_mhz']} MHz x 64 bop"}
+        dtype = "u32"
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hA = [x.cpu().pin_memory() for x in (Ag, Bg, Ab, Bb)]
+        hC = [torch.empty(m * n // 64, dtype=torch.int64).pin_memory() for _ in range(2)]
+        dA = [torch.empty_like(x) for x in (Ag, Bg, Ab, Bb)]
+        dC = [bmm.empty(m, n), bmm.empty(m, n)]
+
+        def e2e_step():
+            for h, d in zip(hA, dA):
+                d.copy_(h, non_blocking=True)
+            step(dA[0], dA[1], dC[0], dA[2], dA[3], dC[1])
+            for h, d in zip(hC, dC):
+                h.copy_(d, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ems], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * bops_step * args.steps / (ems / 1000.0), "unit": "bop/s",
+               "h2d_bytes_per_step": 4 * m * k // 8, "d2h_bytes_per_step": 2 * m * n // 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(n, seed, bool_p)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "bop/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic (seeded SplitMix64 Bernoulli bits)",
+            "config": {"workload": args.workload, "m": m, "k": k, "n": n,
+                       "gf2": f"p=1/2, Strassen depth {depth_g} ({leaves} leaves), "
+                              f"self-inverse alternative basis",
+                       "bool": f"p={bool_p}, cubic", "base_case": _path_name(resolved),
+                       "bool_base_case": _path_name(pb["path"]),
+                       "l2": "inputs larger than L2 (each operand 128 MiB, ~1.7 GB per step)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "phases_ms_per_step": {"base": base_ms / args.steps, "xor": xor_ms / args.steps,
+                                   "transpose": tr_ms / args.steps},
+            "phase_launches": {"base": base_n, "xor": xor_n, "transpose": tr_n},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def _path_name(p) -> str:
+    return {1: "tcgen05 fp8 (e4m3, f32 accumulate)", 2: "tcgen05 int8 (u8, s32 accumulate)",
+            3: "CUDA-core LOP3/POPC"}.get(p, str(p))
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,190 @@
+/*
+ * bmm.h — C ABI of the GB300 (sm_103a) bit-matrix multiplication library.
+ *
+ * Products of bit matrices after Karppa & Kaski, "Engineering Boolean Matrix
+ * Multiplication for Multiple-Accelerator Shared-Memory Architectures"
+ * (arXiv:1909.01554):
+ *   Boolean product  C_ij = OR_k  (A_ik AND B_kj)   over (0,1,OR,AND)  (Sec. 1; Sec. 3.18)
+ *   binary product   C_ij = XOR_k (A_ik AND B_kj)   over GF(2)         (Sec. 2.4; Eq. c-equals-ab)
+ * The binary product may run through the alternative-basis Strassen
+ * recurrences of Sec. 2.2 (self-inverse, Thm. 1) or Sec. 2.3 (chaining,
+ * Thm. 2), or Strassen–Winograd in the standard basis (Sec. 2.1), down to a
+ * cubic base-case block product (Sec. 3.10).
+ *
+ * Matrix layout (all entry points): row-major, bit-packed into uint64 words,
+ * least significant index in the bits of a word (Sec. 3.4 linearisation):
+ * bit j of row i of an R x K matrix is bit (j % 64) of word i*(K/64) + j/64.
+ * So A (m x k) has m*k/64 words, B (k x n) has k*n/64 words, C (m x n) has
+ * m*n/64 words.
+ *
+ * Ownership: every matrix pointer is DEVICE memory owned by the caller, on
+ * the current CUDA device. A and B are read only (the library never writes
+ * them); C is overwritten (not accumulated). Buffers must not overlap.
+ * Alignment: every pointer must be 16-byte aligned (TMA copies need 16 B).
+ *
+ * Execution: asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ * stream). C is valid once the stream has completed. Scratch memory is
+ * allocated stream-ordered (cudaMallocAsync) unless the caller passes one in
+ * bmm_opts.workspace. No entry point falls back to the CPU: failures are
+ * returned as a status.
+ *
+ * Errors: sizes must be positive multiples of 64 (BMM_ERR_INVALID); null or
+ * overlapping pointers give BMM_ERR_INVALID; misaligned pointers give
+ * BMM_ERR_ALIGN. Device-side waits are bounded: a kernel whose wait times out
+ * records it and returns early; bmm_stream_status() then reports
+ * BMM_ERR_TIMEOUT and C is undefined.
+ */
+#ifndef BMM_H
+#define BMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *bmm_stream_t; /* a cudaStream_t */
+
+typedef enum {
+    BMM_OK = 0,
+    BMM_ERR_INVALID = 1,     /* bad size, null/overlapping pointer, bad option */
+    BMM_ERR_ALIGN = 2,       /* pointer not 16-byte aligned */
+    BMM_ERR_NOMEM = 3,       /* scratch allocation failed or caller workspace too small */
+    BMM_ERR_CUDA = 4,        /* a CUDA runtime/driver call failed: bmm_last_cuda_error() */
+    BMM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up; results undefined */
+    BMM_ERR_UNSUPPORTED = 6  /* valid request this build/device does not support */
+} bmm_status;
+
+/* Base-case block product (Sec. 3.10 inner layer). */
+typedef enum {
+    BMM_PATH_AUTO = 0,    /* the fastest path for the shape on this device */
+    BMM_PATH_TC_FP8 = 1,  /* tcgen05 tensor cores, bits -> e4m3, FP32 accumulate */
+    BMM_PATH_TC_I8 = 2,   /* tcgen05 tensor cores, bits -> u8, S32 accumulate */
+    BMM_PATH_POPC = 3     /* CUDA cores: LOP3 AND-XOR / AND-OR over 32-bit words */
+} bmm_path;
+
+/* 2x2 recursion for the binary product. */
+typedef enum {
+    BMM_VARIANT_WINOGRAD = 0,     /* Strassen–Winograd, standard basis (Eqs. sw-*) */
+    BMM_VARIANT_SELF_INVERSE = 1, /* alternative basis, self-inverse (Eqs. mb-*, Thm. 1) */
+    BMM_VARIANT_CHAINING = 2      /* alternative basis, chaining (Eqs. ab-*, Thm. 2) */
+} bmm_variant;
+
+typedef struct {
+    int32_t path;            /* bmm_path */
+    int32_t strassen_depth;  /* -1 auto, 0 cubic, d > 0: d levels (binary product only) */
+    int32_t variant;         /* bmm_variant, used when strassen_depth != 0 */
+    int32_t serial_depth;    /* -1 auto; top levels run depth-first (Sec. 3.8) */
+    void *workspace;         /* optional device scratch; NULL: stream-ordered allocation */
+    uint64_t workspace_bytes;
+} bmm_opts;
+
+/* Fills opts with the defaults (auto path, auto depth, self-inverse variant). */
+void bmm_opts_default(bmm_opts *opts);
+
+/* C = A B over GF(2). A: m x k, B: k x n, C: m x n (Sec. 2.4, Eq. c-equals-ab). */
+bmm_status bmm_gf2(const uint64_t *A, const uint64_t *B, uint64_t *C, int64_t m, int64_t k,
+                   int64_t n, bmm_stream_t stream);
+
+/* C = A B over the Boolean algebra (Sec. 1, Sec. 3.18). Always cubic: the
+ * Boolean semiring has no additive inverse, so no Strassen recursion applies. */
+bmm_status bmm_bool(const uint64_t *A, const uint64_t *B, uint64_t *C, int64_t m, int64_t k,
+                    int64_t n, bmm_stream_t stream);
+
+/* As above with explicit options (opts may be NULL for the defaults). */
+bmm_status bmm_gf2_ex(const uint64_t *A, const uint64_t *B, uint64_t *C, int64_t m, int64_t k,
+                      int64_t n, const bmm_opts *opts, bmm_stream_t stream);
+bmm_status bmm_bool_ex(const uint64_t *A, const uint64_t *B, uint64_t *C, int64_t m, int64_t k,
+                       int64_t n, const bmm_opts *opts, bmm_stream_t stream);
+
+/* Scratch bytes the call with these arguments needs (op: 0 binary, 1 Boolean). */
+bmm_status bmm_workspace_size(int32_t op, int64_t m, int64_t k, int64_t n, const bmm_opts *opts,
+                              uint64_t *bytes);
+
+/* What the planner resolves the options to for these sizes: the base-case
+ * path, the Strassen depth and how many of its top levels run depth-first,
+ * the variant, the number of base-case leaves (7^depth) and the scratch size. */
+typedef struct {
+    int32_t path;
+    int32_t strassen_depth;
+    int32_t serial_depth;
+    int32_t variant;
+    int64_t leaves;
+    uint64_t workspace_bytes;
+} bmm_plan_info;
+bmm_status bmm_plan(int32_t op, int64_t m, int64_t k, int64_t n, const bmm_opts *opts,
+                    bmm_plan_info *info);
+
+/* Batched independent products C_i = A_i B_i, i < count, of individual sizes,
+ * in one persistent launch. The pointer and size arrays are HOST memory; the
+ * matrices are device memory as above. op: 0 binary (cubic), 1 Boolean. */
+bmm_status bmm_gf2_batched(int32_t count, const uint64_t *const *A, const uint64_t *const *B,
+                           uint64_t *const *C, const int64_t *m, const int64_t *k,
+                           const int64_t *n, bmm_stream_t stream);
+bmm_status bmm_bool_batched(int32_t count, const uint64_t *const *A, const uint64_t *const *B,
+                            uint64_t *const *C, const int64_t *m, const int64_t *k,
+                            const int64_t *n, bmm_stream_t stream);
+
+/* ---- the steps of the path, exported for tests and experiments ---------- */
+
+/* Bit transpose: Xt (cols x rows) = X^T (X is rows x cols). The paper
+ * transposes the right operand so both operands run along k (Sec. 3.5). */
+bmm_status bmm_transpose(const uint64_t *X, uint64_t *Xt, int64_t rows, int64_t cols,
+                         bmm_stream_t stream);
+
+/* Base-case product in the "NT" form: C (m x n) = A (m x k) times the
+ * transpose of Bt (n x k), over GF(2) (op 0) or Boolean (op 1), on one path
+ * (Sec. 3.10; Sec. 3.18). */
+bmm_status bmm_base_product(int32_t op, int32_t path, const uint64_t *A, const uint64_t *Bt,
+                            uint64_t *C, int64_t m, int64_t k, int64_t n, bmm_stream_t stream);
+
+/* In-place basis change of X (rows x cols) over `depth` levels of 2x2 blocks:
+ * inverse = 0 applies phi (= psi), inverse = 1 applies chi
+ * (Eqs. mb-fwdbasisrecurrence / mb-revbasisrecurrence for the self-inverse
+ * variant, ab-fwdbasisrecurrence / ab-revbasisrecurrence for chaining; the
+ * identity for Strassen–Winograd). rows, cols divisible by 64 * 2^depth. */
+bmm_status bmm_basis_change(int32_t variant, int32_t inverse, uint64_t *X, int64_t rows,
+                            int64_t cols, int32_t depth, bmm_stream_t stream);
+
+/* ---- tracing -------------------------------------------------------------- */
+
+/* Phases that tracing times separately. */
+typedef enum {
+    BMM_PHASE_BASE = 0,      /* base-case block products (tensor or CUDA-core) */
+    BMM_PHASE_XOR = 1,       /* expand / compress / combine / fold / basis-change passes */
+    BMM_PHASE_TRANSPOSE = 2, /* bit transposes */
+    BMM_PHASE_COUNT = 3
+} bmm_phase;
+
+/* Starts (enable = 1) or stops (0) recording a CUDA event pair around every
+ * kernel launch, on the stream the kernel is launched on. Starting clears
+ * what was recorded before. Process-wide; not for concurrent callers. */
+void bmm_trace_enable(int32_t enable);
+
+/* Synchronises the recorded events and returns, for one phase, how many
+ * kernels were launched and their summed device time in milliseconds. */
+bmm_status bmm_trace_read(int32_t phase, int64_t *launches, double *milliseconds);
+
+/* Kernels launched by this library in this process so far (always counted). */
+int64_t bmm_launch_count(void);
+
+/* ---- status ------------------------------------------------------------- */
+
+/* Synchronises `stream` and reports device-side failures recorded since the
+ * last call (BMM_ERR_TIMEOUT after a bounded wait gave up), else BMM_OK. */
+bmm_status bmm_stream_status(bmm_stream_t stream);
+
+/* Name of a status code (static string). */
+const char *bmm_status_string(bmm_status status);
+
+/* The cudaError_t behind the last BMM_ERR_CUDA on this thread. */
+int32_t bmm_last_cuda_error(void);
+
+/* 1 if the current device can run the tensor-core paths (sm_103), else 0. */
+int32_t bmm_device_supported(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BMM_H */

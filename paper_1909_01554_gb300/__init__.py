@@ -1,0 +1,248 @@
+"""Python binding of libbmm.so: argument marshalling only.
+
+Every step of every product runs in the CUDA kernels behind the C ABI
+(include/bmm.h). There is no CPU fallback: if the library is missing, the
+import of any compute call raises.
+
+Matrices are contiguous torch tensors of dtype int64 on the current CUDA
+device holding the packed uint64 words (row-major, bit j of row i is bit
+j % 64 of word i*(cols/64) + j/64).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbmm.so")
+
+OK, ERR_INVALID, ERR_ALIGN, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+PATH_AUTO, PATH_TC_FP8, PATH_TC_I8, PATH_POPC = 0, 1, 2, 3
+WINOGRAD, SELF_INVERSE, CHAINING = 0, 1, 2
+GF2, BOOL = 0, 1
+
+EXPORTED = [
+    "bmm_opts_default", "bmm_gf2", "bmm_bool", "bmm_gf2_ex", "bmm_bool_ex", "bmm_workspace_size",
+    "bmm_gf2_batched", "bmm_bool_batched", "bmm_transpose", "bmm_base_product",
+    "bmm_basis_change", "bmm_stream_status", "bmm_status_string", "bmm_last_cuda_error",
+    "bmm_device_supported", "bmm_plan", "bmm_trace_enable", "bmm_trace_read", "bmm_launch_count",
+]
+PHASE_BASE, PHASE_XOR, PHASE_TRANSPOSE = 0, 1, 2
+
+
+class BmmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        name = _lib_handle().bmm_status_string(status).decode() if _LIB else str(status)
+        extra = ""
+        if status == ERR_CUDA and _LIB:
+            extra = f" (cudaError {_LIB.bmm_last_cuda_error()})"
+        super().__init__(f"{what}: {name}{extra}")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("strassen_depth", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("serial_depth", ctypes.c_int32),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("strassen_depth", ctypes.c_int32),
+                ("serial_depth", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("leaves", ctypes.c_int64), ("workspace_bytes", ctypes.c_uint64)]
+
+
+_LIB = None
+
+
+def _lib_handle():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        L.bmm_opts_default.argtypes = [ctypes.POINTER(Opts)]
+        L.bmm_opts_default.restype = None
+        for f in (L.bmm_gf2, L.bmm_bool):
+            f.argtypes = [vp, vp, vp, i64, i64, i64, vp]
+            f.restype = i32
+        for f in (L.bmm_gf2_ex, L.bmm_bool_ex):
+            f.argtypes = [vp, vp, vp, i64, i64, i64, ctypes.POINTER(Opts), vp]
+            f.restype = i32
+        L.bmm_workspace_size.argtypes = [i32, i64, i64, i64, ctypes.POINTER(Opts),
+                                         ctypes.POINTER(ctypes.c_uint64)]
+        L.bmm_workspace_size.restype = i32
+        for f in (L.bmm_gf2_batched, L.bmm_bool_batched):
+            f.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp]
+            f.restype = i32
+        L.bmm_transpose.argtypes = [vp, vp, i64, i64, vp]
+        L.bmm_transpose.restype = i32
+        L.bmm_base_product.argtypes = [i32, i32, vp, vp, vp, i64, i64, i64, vp]
+        L.bmm_base_product.restype = i32
+        L.bmm_basis_change.argtypes = [i32, i32, vp, i64, i64, i32, vp]
+        L.bmm_basis_change.restype = i32
+        L.bmm_stream_status.argtypes = [vp]
+        L.bmm_stream_status.restype = i32
+        L.bmm_status_string.argtypes = [i32]
+        L.bmm_status_string.restype = ctypes.c_char_p
+        L.bmm_last_cuda_error.restype = i32
+        L.bmm_device_supported.restype = i32
+        L.bmm_plan.argtypes = [i32, i64, i64, i64, ctypes.POINTER(Opts),
+                               ctypes.POINTER(PlanInfo)]
+        L.bmm_plan.restype = i32
+        L.bmm_trace_enable.argtypes = [i32]
+        L.bmm_trace_enable.restype = None
+        L.bmm_trace_read.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
+        L.bmm_trace_read.restype = i32
+        L.bmm_launch_count.restype = i64
+        _LIB = L
+    return _LIB
+
+
+def lib():
+    """The loaded ctypes handle of libbmm.so."""
+    return _lib_handle()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return 0
+    return t if isinstance(t, int) else t.data_ptr()
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise BmmError(status, what)
+
+
+def opts(path: int | None = None, depth: int | None = None, variant: int | None = None,
+         serial: int | None = None, workspace=None, workspace_bytes: int = 0) -> Opts:
+    o = Opts()
+    _lib_handle().bmm_opts_default(ctypes.byref(o))
+    if path is not None:
+        o.path = path
+    if depth is not None:
+        o.strassen_depth = depth
+    if variant is not None:
+        o.variant = variant
+    if serial is not None:
+        o.serial_depth = serial
+    if workspace is not None:
+        o.workspace = _ptr(workspace)
+        o.workspace_bytes = workspace_bytes
+    return o
+
+
+def empty(rows: int, cols: int, device="cuda"):
+    """An uninitialised packed rows x cols bit matrix on the device."""
+    import torch
+
+    return torch.empty(rows * cols // 64, dtype=torch.int64, device=device)
+
+
+def gf2(A, B, C, m: int, k: int, n: int, stream=None, **kw) -> None:
+    """C = A B over GF(2)."""
+    L = _lib_handle()
+    if kw:
+        o = opts(**kw)
+        _check(L.bmm_gf2_ex(_ptr(A), _ptr(B), _ptr(C), m, k, n, ctypes.byref(o), _stream(stream)),
+               "bmm_gf2_ex")
+    else:
+        _check(L.bmm_gf2(_ptr(A), _ptr(B), _ptr(C), m, k, n, _stream(stream)), "bmm_gf2")
+
+
+def boolean(A, B, C, m: int, k: int, n: int, stream=None, **kw) -> None:
+    """C = A B over the Boolean algebra."""
+    L = _lib_handle()
+    if kw:
+        o = opts(**kw)
+        _check(L.bmm_bool_ex(_ptr(A), _ptr(B), _ptr(C), m, k, n, ctypes.byref(o),
+                             _stream(stream)), "bmm_bool_ex")
+    else:
+        _check(L.bmm_bool(_ptr(A), _ptr(B), _ptr(C), m, k, n, _stream(stream)), "bmm_bool")
+
+
+def product(op: int, A, B, C, m: int, k: int, n: int, stream=None, **kw) -> None:
+    (gf2 if op == GF2 else boolean)(A, B, C, m, k, n, stream=stream, **kw)
+
+
+def workspace_size(op: int, m: int, k: int, n: int, **kw) -> int:
+    o = opts(**kw)
+    out = ctypes.c_uint64(0)
+    _check(_lib_handle().bmm_workspace_size(op, m, k, n, ctypes.byref(o), ctypes.byref(out)),
+           "bmm_workspace_size")
+    return int(out.value)
+
+
+def plan(op: int, m: int, k: int, n: int, **kw) -> dict:
+    """The planner's resolution of the options for these sizes."""
+    o = opts(**kw)
+    info = PlanInfo()
+    _check(_lib_handle().bmm_plan(op, m, k, n, ctypes.byref(o), ctypes.byref(info)), "bmm_plan")
+    return {f: int(getattr(info, f)) for f, _ in PlanInfo._fields_}
+
+
+def transpose(X, Xt, rows: int, cols: int, stream=None) -> None:
+    _check(_lib_handle().bmm_transpose(_ptr(X), _ptr(Xt), rows, cols, _stream(stream)),
+           "bmm_transpose")
+
+
+def base_product(op: int, path: int, A, Bt, C, m: int, k: int, n: int, stream=None) -> None:
+    """C = A Bt^T (the base case in NT form) on one path."""
+    _check(_lib_handle().bmm_base_product(op, path, _ptr(A), _ptr(Bt), _ptr(C), m, k, n,
+                                          _stream(stream)), "bmm_base_product")
+
+
+def basis_change(variant: int, inverse: bool, X, rows: int, cols: int, depth: int,
+                 stream=None) -> None:
+    _check(_lib_handle().bmm_basis_change(variant, int(inverse), _ptr(X), rows, cols, depth,
+                                          _stream(stream)), "bmm_basis_change")
+
+
+def batched(op: int, As, Bs, Cs, ms, ks, ns, stream=None) -> None:
+    """C_i = A_i B_i for every i, in one persistent launch (host pointer arrays)."""
+    count = len(As)
+    P = ctypes.c_void_p * count
+    I = ctypes.c_int64 * count
+    a, b, c = P(*map(_ptr, As)), P(*map(_ptr, Bs)), P(*map(_ptr, Cs))
+    mm, kk, nn = I(*ms), I(*ks), I(*ns)
+    f = _lib_handle().bmm_gf2_batched if op == GF2 else _lib_handle().bmm_bool_batched
+    _check(f(count, a, b, c, mm, kk, nn, _stream(stream)), "bmm_batched")
+
+
+def stream_status(stream=None) -> None:
+    """Synchronise the stream and raise if a device-side wait timed out."""
+    _check(_lib_handle().bmm_stream_status(_stream(stream)), "bmm_stream_status")
+
+
+def device_supported() -> bool:
+    return bool(_lib_handle().bmm_device_supported())
+
+
+def trace_enable(on: bool) -> None:
+    """Record a CUDA event pair around every library kernel launch (or stop)."""
+    _lib_handle().bmm_trace_enable(int(on))
+
+
+def trace_read(phase: int) -> tuple[int, float]:
+    """(launches, summed device milliseconds) recorded for one phase."""
+    n = ctypes.c_int64(0)
+    ms = ctypes.c_double(0.0)
+    _check(_lib_handle().bmm_trace_read(phase, ctypes.byref(n), ctypes.byref(ms)),
+           "bmm_trace_read")
+    return int(n.value), float(ms.value)
+
+
+def launch_count() -> int:
+    return int(_lib_handle().bmm_launch_count())

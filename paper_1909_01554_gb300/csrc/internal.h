@@ -1,0 +1,60 @@
+// Internal declarations shared by the translation units of libbmm.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bmm.h"
+
+namespace bmm {
+
+constexpr int OP_GF2 = 0;
+constexpr int OP_BOOL = 1;
+
+// Device-side failure word (one per device, allocated on first use). Kernels
+// whose bounded waits give up OR a code into it and return.
+constexpr uint32_t DEVERR_TIMEOUT = 1u;
+
+uint32_t* device_error_word();  // nullptr if allocation failed
+
+// Records a CUDA error for bmm_last_cuda_error() and maps it to a status.
+bmm_status cuda_fail(cudaError_t e);
+#define BMM_CUDA_TRY(expr)                              \
+    do {                                                \
+        cudaError_t bmm_e_ = (expr);                    \
+        if (bmm_e_ != cudaSuccess) return cuda_fail(bmm_e_); \
+    } while (0)
+
+// Tracing hooks: wrap every kernel launch in a TraceScope.
+void trace_launch_begin(int phase, cudaStream_t s, void** token);
+void trace_launch_end(void* token, cudaStream_t s);
+struct TraceScope {
+    void* tok = nullptr;
+    cudaStream_t s;
+    TraceScope(int phase, cudaStream_t st) : s(st) { trace_launch_begin(phase, s, &tok); }
+    ~TraceScope() { trace_launch_end(tok, s); }
+};
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+// Compute capability major*10 + minor of the current device.
+int device_cc();
+
+// ---- launchers (each returns a launch error, or cudaSuccess) -------------
+cudaError_t launch_transpose(const uint64_t* X, uint64_t* Xt, int64_t rows, int64_t cols,
+                             cudaStream_t s);
+// X is rows x cols with row pitch `pitch` words; Xt is cols x rows, row pitch tpitch words.
+cudaError_t launch_transpose_pitched(const uint64_t* X, int64_t pitch, uint64_t* Xt,
+                                     int64_t tpitch, int64_t rows, int64_t cols,
+                                     cudaStream_t s);
+
+// CUDA-core base case: C (m x n, row pitch ldc words) = A (m x k, pitch lda)
+// times Bt^T (Bt n x k, pitch ldb), GF(2) or Boolean.
+// Leaf h of a batch of `count` starts at A + h*strideA, Bt + h*strideB,
+// C + h*strideC (words).
+cudaError_t launch_popc_nt(int op, const uint64_t* A, int64_t lda, int64_t strideA,
+                           const uint64_t* Bt, int64_t ldb, int64_t strideB, uint64_t* C,
+                           int64_t ldc, int64_t strideC, int64_t count, int64_t m, int64_t k,
+                           int64_t n, cudaStream_t s);
+
+}  // namespace bmm

@@ -1,0 +1,228 @@
+// Planner and executor for one product (the accelerator-side layers of
+// Sec. 3.4 on a single GPU with all operands resident in HBM):
+//   transpose B -> Bt (Sec. 3.5), then `serial` depth-first levels
+//   (Sec. 3.8: combine, recurse, fold, reusing scratch across the 7
+//   branches), then `depth - serial` breadth-first levels merged into one
+//   expanding pass per operand (Sec. 3.9, 3.15), the batched base case over
+//   the 7^d leaves (Sec. 3.10), and one compressing pass (Sec. 3.11).
+#include <cstring>
+
+#include "plan.h"
+#include "slp.h"
+
+namespace bmm {
+
+cudaError_t launch_expand(int variant, int operand, int d, const uint64_t* X, int64_t pitch,
+                          int64_t rows, int64_t wcols, uint64_t* leaves, cudaStream_t s);
+cudaError_t launch_compress(int variant, int d, const uint64_t* leaves, int64_t lr, int64_t lw,
+                            uint64_t* C, int64_t ldc, cudaStream_t s);
+cudaError_t launch_combine(int operand, const uint64_t* X, int64_t pitch, int64_t hr, int64_t hw,
+                           uint32_t mask, uint64_t* dst, cudaStream_t s);
+cudaError_t launch_fold(const uint64_t* R, int64_t hr, int64_t hw, uint64_t* C, int64_t ldc,
+                        uint32_t dest, uint32_t first, cudaStream_t s);
+bool tc_path_available();
+bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int64_t strideA,
+                          const uint64_t* Bt, int64_t ldb, int64_t strideB, uint64_t* C,
+                          int64_t ldc, int64_t strideC, int64_t count, int64_t m, int64_t k,
+                          int64_t n, cudaStream_t s);
+
+namespace {
+
+constexpr uint64_t ALIGN = 256;
+uint64_t round_up(uint64_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+constexpr int MAX_MERGED = 2;  // breadth-first levels merged in registers
+
+int ipow7(int d) {
+    int r = 1;
+    while (d-- > 0) r *= 7;
+    return r;
+}
+
+bool divisible(int64_t m, int64_t k, int64_t n, int d) {
+    const int64_t unit = (int64_t)64 << d;
+    return (m % ((int64_t)1 << d) == 0) && (m >> d) % 64 == 0 && k % unit == 0 && n % unit == 0;
+}
+
+// Bytes of scratch for a plan: Bt, the depth-first branch buffers of every
+// serial level, and the breadth-first leaves at the bottom.
+uint64_t workspace_for(int64_t m, int64_t k, int64_t n, int depth, int serial) {
+    uint64_t b = round_up((uint64_t)k * n / 8);  // Bt
+    for (int l = 1; l <= serial; l++) {
+        b += round_up((uint64_t)(m >> l) * (k >> l) / 8);
+        b += round_up((uint64_t)(n >> l) * (k >> l) / 8);
+        b += round_up((uint64_t)(m >> l) * (n >> l) / 8);
+    }
+    const int dp = depth - serial;
+    if (dp > 0) {
+        const uint64_t r = (uint64_t)ipow7(dp);
+        b += round_up(r * (uint64_t)(m >> depth) * (k >> depth) / 8);
+        b += round_up(r * (uint64_t)(n >> depth) * (k >> depth) / 8);
+        b += round_up(r * (uint64_t)(m >> depth) * (n >> depth) / 8);
+    }
+    return b;
+}
+
+struct Exec {
+    const Plan& p;
+    char* ws;
+    cudaStream_t s;
+    uint32_t xi[7], eta[7], zeta[4];
+    uint64_t* Bt = nullptr;
+    uint64_t* T[8] = {nullptr};
+    uint64_t* S[8] = {nullptr};
+    uint64_t* R[8] = {nullptr};
+    uint64_t *TL = nullptr, *SL = nullptr, *QL = nullptr;
+
+    Exec(const Plan& plan, void* w, cudaStream_t st) : p(plan), ws((char*)w), s(st) {
+        switch (p.variant) {
+            case 0: slp::level_masks<0>(xi, eta, zeta); break;
+            case 1: slp::level_masks<1>(xi, eta, zeta); break;
+            default: slp::level_masks<2>(xi, eta, zeta); break;
+        }
+        uint64_t off = 0;
+        auto take = [&](uint64_t bytes) {
+            uint64_t* q = (uint64_t*)(ws + off);
+            off += round_up(bytes);
+            return q;
+        };
+        Bt = take((uint64_t)p.k * p.n / 8);
+        for (int l = 1; l <= p.serial; l++) {
+            T[l] = take((uint64_t)(p.m >> l) * (p.k >> l) / 8);
+            S[l] = take((uint64_t)(p.n >> l) * (p.k >> l) / 8);
+            R[l] = take((uint64_t)(p.m >> l) * (p.n >> l) / 8);
+        }
+        const int dp = p.depth - p.serial;
+        if (dp > 0) {
+            const uint64_t r = (uint64_t)ipow7(dp);
+            TL = take(r * (uint64_t)(p.m >> p.depth) * (p.k >> p.depth) / 8);
+            SL = take(r * (uint64_t)(p.n >> p.depth) * (p.k >> p.depth) / 8);
+            QL = take(r * (uint64_t)(p.m >> p.depth) * (p.n >> p.depth) / 8);
+        }
+    }
+
+    bmm_status level(int l, const uint64_t* A, int64_t lda, const uint64_t* B, int64_t ldb,
+                     uint64_t* C, int64_t ldc, int64_t m, int64_t k, int64_t n) {
+        if (l < p.serial) {
+            const int64_t hm = m / 2, hk = k / 2, hn = n / 2;
+            uint32_t first = 0xF;
+            for (int h = 0; h < 7; h++) {
+                BMM_CUDA_TRY(launch_combine(0, A, lda, hm, hk / 64, xi[h], T[l + 1], s));
+                BMM_CUDA_TRY(launch_combine(1, B, ldb, hn, hk / 64, eta[h], S[l + 1], s));
+                bmm_status st = level(l + 1, T[l + 1], hk / 64, S[l + 1], hk / 64, R[l + 1],
+                                      hn / 64, hm, hk, hn);
+                if (st != BMM_OK) return st;
+                uint32_t dest = 0;
+                for (int q = 0; q < 4; q++) dest |= ((zeta[q] >> h) & 1u) << q;
+                if (dest) {
+                    BMM_CUDA_TRY(launch_fold(R[l + 1], hm, hn / 64, C, ldc, dest, first & dest, s));
+                    first &= ~dest;
+                }
+            }
+            return BMM_OK;
+        }
+        const int dp = p.depth - l;
+        if (dp == 0)
+            return run_base_product(p.op, p.path, A, lda, B, ldb, C, ldc, m, k, n, s);
+        const int64_t lm = m >> dp, lk = k >> dp, ln = n >> dp;
+        BMM_CUDA_TRY(launch_expand(p.variant, 0, dp, A, lda, m, k / 64, TL, s));
+        BMM_CUDA_TRY(launch_expand(p.variant, 1, dp, B, ldb, n, k / 64, SL, s));
+        const int64_t leaves = ipow7(dp);
+        bmm_status st = run_base_product_batched(p.op, p.path, TL, lk / 64, lm * lk / 64, SL,
+                                                 lk / 64, ln * lk / 64, QL, ln / 64, lm * ln / 64,
+                                                 leaves, lm, lk, ln, s);
+        if (st != BMM_OK) return st;
+        BMM_CUDA_TRY(launch_compress(p.variant, dp, QL, lm, ln / 64, C, ldc, s));
+        return BMM_OK;
+    }
+};
+
+}  // namespace
+
+bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* opts, Plan* out) {
+    bmm_opts o;
+    bmm_opts_default(&o);
+    if (opts) o = *opts;
+    Plan p;
+    p.op = op;
+    p.m = m;
+    p.k = k;
+    p.n = n;
+    if (o.variant < 0 || o.variant > 2) return BMM_ERR_INVALID;
+    p.variant = o.variant;
+    if (o.path < BMM_PATH_AUTO || o.path > BMM_PATH_POPC) return BMM_ERR_INVALID;
+    if (o.path != BMM_PATH_AUTO && o.path != BMM_PATH_POPC && !tc_path_available())
+        return BMM_ERR_UNSUPPORTED;
+    // recursion depth
+    if (op == OP_BOOL) {
+        if (o.strassen_depth > 0) return BMM_ERR_INVALID;  // no additive inverse
+        p.depth = 0;
+    } else if (o.strassen_depth >= 0) {
+        p.depth = o.strassen_depth;
+        if (p.depth > 6) return BMM_ERR_UNSUPPORTED;
+        if (p.depth > 0 && !divisible(m, k, n, p.depth)) return BMM_ERR_UNSUPPORTED;
+    } else {
+        // Auto: recurse while every leaf dimension stays >= 8192 (below that the
+        // base case loses efficiency faster than 7/8 of the work is saved).
+        int d = 0;
+        while (d < 4 && divisible(m, k, n, d + 1) && (m >> (d + 1)) >= 8192 &&
+               (k >> (d + 1)) >= 8192 && (n >> (d + 1)) >= 8192)
+            d++;
+        p.depth = d;
+    }
+    // base-case path: the tensor cores whenever the leaves allow TMA tiles
+    // (k of a leaf a multiple of 128 bits), else the CUDA-core kernel.
+    if (o.path == BMM_PATH_AUTO)
+        p.path = (tc_path_available() && ((k >> p.depth) % 128) == 0) ? BMM_PATH_TC_FP8
+                                                                        : BMM_PATH_POPC;
+    else
+        p.path = o.path;
+    // depth-first levels: at least depth - MAX_MERGED; more while the
+    // breadth-first scratch does not fit in free device memory.
+    int serial_min = p.depth > MAX_MERGED ? p.depth - MAX_MERGED : 0;
+    if (o.serial_depth >= 0) {
+        if (o.serial_depth > p.depth) return BMM_ERR_INVALID;
+        p.serial = o.serial_depth < serial_min ? serial_min : o.serial_depth;
+    } else {
+        p.serial = serial_min;
+        size_t fr = 0, tot = 0;
+        if (!(o.workspace) && cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+            while (p.serial < p.depth &&
+                   workspace_for(m, k, n, p.depth, p.serial) > (uint64_t)(fr * 0.9))
+                p.serial++;
+        }
+    }
+    p.workspace_bytes = workspace_for(m, k, n, p.depth, p.serial);
+    *out = p;
+    return BMM_OK;
+}
+
+bmm_status execute_plan(const Plan& p, const uint64_t* A, const uint64_t* B, uint64_t* C,
+                        void* workspace, cudaStream_t s) {
+    Exec ex(p, workspace, s);
+    BMM_CUDA_TRY(launch_transpose(B, ex.Bt, p.k, p.n, s));
+    return ex.level(0, A, p.k / 64, ex.Bt, p.k / 64, C, p.n / 64, p.m, p.k, p.n);
+}
+
+bmm_status run_base_product(int op, int path, const uint64_t* A, int64_t lda, const uint64_t* Bt,
+                            int64_t ldb, uint64_t* C, int64_t ldc, int64_t m, int64_t k,
+                            int64_t n, cudaStream_t s) {
+    return run_base_product_batched(op, path, A, lda, 0, Bt, ldb, 0, C, ldc, 0, 1, m, k, n, s);
+}
+
+bmm_status run_base_product_batched(int op, int path, const uint64_t* A, int64_t lda,
+                                    int64_t strideA, const uint64_t* Bt, int64_t ldb,
+                                    int64_t strideB, uint64_t* C, int64_t ldc, int64_t strideC,
+                                    int64_t count, int64_t m, int64_t k, int64_t n,
+                                    cudaStream_t s) {
+    if (count <= 0) return BMM_OK;
+    if (path == BMM_PATH_POPC) {
+        BMM_CUDA_TRY(launch_popc_nt(op, A, lda, strideA, Bt, ldb, strideB, C, ldc, strideC, count,
+                                    m, k, n, s));
+        return BMM_OK;
+    }
+    return run_tc_strided(op, path, A, lda, strideA, Bt, ldb, strideB, C, ldc, strideC, count, m,
+                          k, n, s);
+}
+
+}  // namespace bmm

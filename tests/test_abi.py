@@ -1,0 +1,70 @@
+"""The C-ABI library loads and exports every symbol include/bmm.h declares
+(no compute calls: these run without a GPU)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "bmm.h")
+LIB = os.path.join(ROOT, "paper_1909_01554_gb300", "libbmm.so")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(bmm_[a-z0-9_]+)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    if not os.path.exists(LIB):
+        from paper_1909_01554_gb300 import build
+
+        build.build()
+    return LIB
+
+
+def test_header_declares_the_product_calls():
+    names = declared_functions()
+    for required in ("bmm_gf2", "bmm_bool", "bmm_gf2_batched", "bmm_bool_batched",
+                     "bmm_base_product", "bmm_transpose", "bmm_basis_change"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", built_lib], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_names_match(built_lib):
+    import paper_1909_01554_gb300 as bmm
+
+    L = bmm.lib()
+    for name in declared_functions():
+        assert hasattr(L, name)
+    assert set(bmm.EXPORTED) <= set(declared_functions())
+    assert L.bmm_status_string(bmm.ERR_TIMEOUT) == b"BMM_ERR_TIMEOUT"
+
+
+def test_argument_checks_need_no_gpu(built_lib):
+    """Invalid sizes and null pointers are rejected before any CUDA call."""
+    import paper_1909_01554_gb300 as bmm
+
+    L = bmm.lib()
+    assert L.bmm_gf2(0, 0, 0, 64, 64, 64, None) == bmm.ERR_INVALID
+    assert L.bmm_gf2(16, 32, 4096, 100, 64, 64, None) == bmm.ERR_INVALID
+    assert L.bmm_bool(16, 32, 4096, 64, 0, 64, None) == bmm.ERR_INVALID
+    assert L.bmm_gf2(8, 32 << 20, 64 << 20, 64, 64, 64, None) == bmm.ERR_ALIGN
+    # C overlapping A
+    assert L.bmm_gf2(1 << 20, 32 << 20, (1 << 20) + 256, 64, 64, 64, None) == bmm.ERR_INVALID
+    assert L.bmm_transpose(0, 16, 64, 64, None) == bmm.ERR_INVALID
+    assert L.bmm_basis_change(1, 0, 16, 96, 128, 1, None) == bmm.ERR_INVALID
+    assert L.bmm_basis_change(7, 0, 16, 128, 128, 1, None) == bmm.ERR_INVALID

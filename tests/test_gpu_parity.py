@@ -1,0 +1,213 @@
+"""GPU path against the CPU oracle, bit for bit, through the C ABI.
+
+Sizes span several tiles with ragged tails (multiples of 64 that are not
+multiples of the 128/256 tile sizes), degenerate inputs (zero, identity,
+all ones), every base-case path, every Strassen variant and depth split."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import first_mismatch, from_dev, gen, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU machine
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_1909_01554_gb300 as bmm  # noqa: E402
+
+OPS = {bmm.GF2: O.GF2, bmm.BOOL: O.BOOL}
+
+
+def paths():
+    ps = [bmm.PATH_POPC]
+    if bmm.device_supported():
+        ps.append(bmm.PATH_TC_FP8)
+    return ps
+
+
+def run(op, Ah, Bh, m, k, n, **kw):
+    dA, dB = to_dev(Ah), to_dev(Bh)
+    dC = bmm.empty(m, n)
+    dC.fill_(-1)
+    bmm.product(op, dA, dB, dC, m, k, n, **kw)
+    bmm.stream_status()
+    return from_dev(dC, m, n)
+
+
+def check(got, want, what):
+    mm = first_mismatch(got, want)
+    assert mm is None, f"{what}: first mismatch (row, word, got, want, count) = {mm}"
+
+
+# ------------------------------------------------------------ transpose
+@pytest.mark.parametrize("rows,cols", [(64, 64), (256, 512), (320, 192), (4096, 128), (64, 1344)])
+def test_transpose(rows, cols):
+    X = gen(rows, cols, 3, 0)
+    dX = to_dev(X)
+    dT = bmm.empty(cols, rows)
+    bmm.transpose(dX, dT, rows, cols)
+    bmm.stream_status()
+    check(from_dev(dT, cols, rows), O.transpose(X, rows, cols), "transpose")
+
+
+# ------------------------------------------------------------ base case
+@pytest.mark.parametrize("path", paths())
+@pytest.mark.parametrize("op", [bmm.GF2, bmm.BOOL])
+@pytest.mark.parametrize("m,k,n", [(64, 64, 64), (128, 256, 256), (192, 320, 448),
+                                   (384, 1152, 320), (1024, 2048, 1024)])
+def test_base_product(path, op, m, k, n):
+    if path != bmm.PATH_POPC and k % 128:
+        pytest.skip("tensor paths need k % 128 == 0 (TMA row pitch)")
+    p = None if op == bmm.GF2 else "1/16"
+    Ah, Bh = gen(m, k, 5, 0, p), gen(k, n, 5, 1, p)
+    Bt = O.transpose(Bh, k, n)
+    dC = bmm.empty(m, n)
+    dC.fill_(-1)
+    bmm.base_product(op, path, to_dev(Ah), to_dev(Bt), dC, m, k, n)
+    bmm.stream_status()
+    check(from_dev(dC, m, n), O.cubic(OPS[op], Ah, Bh, m, k, n), f"base op={op} path={path}")
+
+
+@pytest.mark.parametrize("path", paths())
+def test_base_product_counts_cover_every_parity(path):
+    """Row i of A has its first c_i bits set and B is all ones: entry (i, j) of the
+    integer product is c_i for every j, so c_i = 0..k exercises every count."""
+    m, k, n = 256, 1024, 256
+    c = np.array([(37 * i) % (k + 1) for i in range(m)])
+    Ab = (np.arange(k)[None, :] < c[:, None]).astype(np.uint8)
+    Ah = O.pack(Ab)
+    Bt = O.pack(np.ones((n, k), dtype=np.uint8))
+    for op in (bmm.GF2, bmm.BOOL):
+        dC = bmm.empty(m, n)
+        bmm.base_product(op, path, to_dev(Ah), to_dev(Bt), dC, m, k, n)
+        bmm.stream_status()
+        want = O.cubic(OPS[op], Ah, O.transpose(Bt, n, k), m, k, n)
+        check(from_dev(dC, m, n), want, f"counts op={op} path={path}")
+
+
+@pytest.mark.parametrize("path", paths())
+def test_base_product_all_ones_large_k(path):
+    """All-ones operands: every count equals k (the largest count a run reaches)."""
+    m, n = 128, 256
+    for k in (8192, 65536 + 128):
+        if path != bmm.PATH_POPC and k % 128:
+            continue
+        Ah = np.full((m, k // 64), np.uint64(0xFFFFFFFFFFFFFFFF))
+        Bt = np.full((n, k // 64), np.uint64(0xFFFFFFFFFFFFFFFF))
+        for op in (bmm.GF2, bmm.BOOL):
+            dC = bmm.empty(m, n)
+            bmm.base_product(op, path, to_dev(Ah), to_dev(Bt), dC, m, k, n)
+            bmm.stream_status()
+            want = (k % 2) if op == bmm.GF2 else 1
+            got = O.unpack(from_dev(dC, m, n), m, n)
+            assert (got == want).all(), f"k={k} op={op} path={path}"
+
+
+# ------------------------------------------------------------ full products
+@pytest.mark.parametrize("op", [bmm.GF2, bmm.BOOL])
+@pytest.mark.parametrize("m,k,n", [(64, 128, 64), (448, 320, 576), (1024, 1024, 1024)])
+def test_cubic_product(op, m, k, n):
+    p = None if op == bmm.GF2 else "1/32"
+    Ah, Bh = gen(m, k, 7, 0, p), gen(k, n, 7, 1, p)
+    for path in paths():
+        if path != bmm.PATH_POPC and k % 128:
+            continue
+        got = run(op, Ah, Bh, m, k, n, path=path, depth=0)
+        check(got, O.cubic(OPS[op], Ah, Bh, m, k, n), f"cubic op={op} path={path}")
+
+
+def test_identity_and_zero():
+    n = 512
+    I = O.pack(np.eye(n, dtype=np.uint8))
+    A = gen(n, n, 9, 0)
+    Z = np.zeros_like(A)
+    for op in (bmm.GF2, bmm.BOOL):
+        check(run(op, A, I, n, n, n), A, "A I")
+        check(run(op, I, A, n, n, n), A, "I A")
+        check(run(op, A, Z, n, n, n), Z, "A 0")
+
+
+def test_config1_4096_full_compare():
+    """m = k = n = 4096: GF(2) with p = 1/2, Boolean with p = 1/64, seed 1."""
+    n = 4096
+    A, B = gen(n, n, 1, 0), gen(n, n, 1, 1)
+    Ab, Bb = gen(n, n, 1, 0, "1/64"), gen(n, n, 1, 1, "1/64")
+    want_g = O.cubic(O.GF2, A, B, n, n, n)
+    want_b = O.cubic(O.BOOL, Ab, Bb, n, n, n)
+    for path in paths():
+        check(run(bmm.GF2, A, B, n, n, n, path=path, depth=0), want_g, f"gf2 path={path}")
+        check(run(bmm.BOOL, Ab, Bb, n, n, n, path=path), want_b, f"bool path={path}")
+    density = O.unpack(want_b, n, n).mean()
+    assert abs(density - (1 - np.exp(-1))) < 0.01
+
+
+# ------------------------------------------------------------ Strassen
+@pytest.mark.parametrize("variant", [bmm.WINOGRAD, bmm.SELF_INVERSE, bmm.CHAINING])
+@pytest.mark.parametrize("depth,serial", [(1, 0), (2, 0), (1, 1), (2, 1), (3, 1), (3, 2)])
+def test_strassen_variants(variant, depth, serial):
+    m, k, n = 1024, 2048, 1536
+    if depth == 3:
+        m, k, n = 2048, 2048, 1024
+    Ah, Bh = gen(m, k, 13, 0), gen(k, n, 13, 1)
+    want = O.cubic(O.GF2, Ah, Bh, m, k, n)
+    got = run(bmm.GF2, Ah, Bh, m, k, n, depth=depth, serial=serial, variant=variant,
+              path=bmm.PATH_POPC)
+    check(got, want, f"strassen v={variant} d={depth} s={serial}")
+
+
+@pytest.mark.parametrize("path", paths())
+def test_strassen_over_each_base_case(path):
+    n = 2048
+    Ah, Bh = gen(n, n, 17, 0), gen(n, n, 17, 1)
+    want = O.cubic(O.GF2, Ah, Bh, n, n, n)
+    check(run(bmm.GF2, Ah, Bh, n, n, n, depth=2, path=path), want, f"strassen path={path}")
+
+
+@pytest.mark.parametrize("variant", [bmm.SELF_INVERSE, bmm.CHAINING])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_basis_change_matches_oracle(variant, inverse):
+    rows, cols, d = 1024, 2048, 3
+    X = gen(rows, cols, 19, 0)
+    dX = to_dev(X)
+    bmm.basis_change(variant, inverse, dX, rows, cols, d)
+    bmm.stream_status()
+    want, _ = O.basis_change(variant, inverse, X, rows, cols, d)
+    check(from_dev(dX, rows, cols), want, "basis change")
+
+
+def test_errors_are_reported():
+    dA = bmm.empty(128, 128)
+    dC = bmm.empty(128, 128)
+    with pytest.raises(bmm.BmmError) as e:
+        bmm.boolean(dA, dA, dC, 128, 128, 128, depth=1)
+    assert e.value.status == bmm.ERR_INVALID
+    with pytest.raises(bmm.BmmError) as e:
+        bmm.gf2(dA, dA, dC, 128, 128, 128, depth=3)
+    assert e.value.status == bmm.ERR_UNSUPPORTED
+    with pytest.raises(bmm.BmmError) as e:
+        bmm.gf2(dA.data_ptr() + 8, dA, dC, 64, 64, 64)
+    assert e.value.status == bmm.ERR_ALIGN
+    with pytest.raises(bmm.BmmError) as e:
+        bmm.gf2(dA, dA, dA, 128, 128, 128)
+    assert e.value.status == bmm.ERR_INVALID
+
+
+def test_int8_tensor_path_is_unsupported_on_sm103():
+    """sm_103a has no 8-bit integer tensor-core MMA: the path reports UNSUPPORTED."""
+    d = bmm.empty(128, 128)
+    c = bmm.empty(128, 128)
+    with pytest.raises(bmm.BmmError) as e:
+        bmm.base_product(bmm.GF2, bmm.PATH_TC_I8, d, d, c, 128, 128, 128)
+    assert e.value.status == bmm.ERR_UNSUPPORTED
+
+
+def test_device_generator_matches_cpu_generator():
+    import bitgen
+
+    for p in (None, "2^-7.5", "1/64"):
+        t = bmm.empty(192, 640)
+        bitgen.fill_device(t, 640, 23, 1, p=p, stream=torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert (from_dev(t, 192, 640) == gen(192, 640, 23, 1, p)).all()

@@ -146,6 +146,33 @@ bmm_status bmm_base_product(int32_t op, int32_t path, const uint64_t *A, const u
 bmm_status bmm_basis_change(int32_t variant, int32_t inverse, uint64_t *X, int64_t rows,
                             int64_t cols, int32_t depth, bmm_stream_t stream);
 
+/* ---- fixed-scratch product ------------------------------------------------ */
+
+/* Bytes of the device array bmm_product_noalloc uses as scratch. */
+#define BMM_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* C = A B, cubic, over GF(2) (op 0) or the Boolean algebra (op 1), with the
+ * same layouts, alignment and argument checks as bmm_gf2 / bmm_bool, but
+ * without allocating any memory. The paper has no counterpart: this entry
+ * point is for callers that cannot allocate device memory while they run,
+ * such as applications whose framework reserves nearly all of HBM in its
+ * own pool (a library allocation could fail or fragment it), latency-bound
+ * loops in which an allocation might synchronise the device, and
+ * deployments that fix all device memory when the library is loaded.
+ *
+ * Its only scratch, the transpose of B (k x n bits), lives in one static
+ * device array of BMM_NOALLOC_SCRATCH_BYTES bytes that every GPU loading
+ * this library keeps until the process exits. Sizes with k*n/8 larger than
+ * that return BMM_ERR_NOMEM. The first call on each device looks the array's
+ * address up (cudaGetSymbolAddress); make that first call before any stream
+ * capture begins. All calls share the one array and it keeps the last call's
+ * contents; each call writes every word it later reads, so nothing needs
+ * clearing, but calls whose work overlaps on the GPU (for example on two
+ * streams at once) race on it and must be serialised by the caller. With
+ * tracing on (bmm_trace_enable), launches also create CUDA events. */
+bmm_status bmm_product_noalloc(int32_t op, const uint64_t *A, const uint64_t *B, uint64_t *C,
+                               int64_t m, int64_t k, int64_t n, bmm_stream_t stream);
+
 /* ---- tracing -------------------------------------------------------------- */
 
 /* Phases that tracing times separately. */

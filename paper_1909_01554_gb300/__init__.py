@@ -25,7 +25,7 @@ EXPORTED = [
     "bmm_opts_default", "bmm_gf2", "bmm_bool", "bmm_gf2_ex", "bmm_bool_ex", "bmm_workspace_size",
     "bmm_gf2_batched", "bmm_bool_batched", "bmm_transpose", "bmm_base_product",
     "bmm_basis_change", "bmm_stream_status", "bmm_status_string", "bmm_last_cuda_error",
-    "bmm_device_supported", "bmm_plan", "bmm_trace_enable", "bmm_trace_read", "bmm_launch_count",
+    "bmm_device_supported", "bmm_plan", "bmm_product_noalloc", "bmm_trace_enable", "bmm_trace_read", "bmm_launch_count",
 ]
 PHASE_BASE, PHASE_XOR, PHASE_TRANSPOSE = 0, 1, 2
 
@@ -91,6 +91,8 @@ def _lib_handle():
         L.bmm_plan.argtypes = [i32, i64, i64, i64, ctypes.POINTER(Opts),
                                ctypes.POINTER(PlanInfo)]
         L.bmm_plan.restype = i32
+        L.bmm_product_noalloc.argtypes = [i32, vp, vp, vp, i64, i64, i64, vp]
+        L.bmm_product_noalloc.restype = i32
         L.bmm_trace_enable.argtypes = [i32]
         L.bmm_trace_enable.restype = None
         L.bmm_trace_read.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
@@ -175,6 +177,12 @@ def boolean(A, B, C, m: int, k: int, n: int, stream=None, **kw) -> None:
 
 def product(op: int, A, B, C, m: int, k: int, n: int, stream=None, **kw) -> None:
     (gf2 if op == GF2 else boolean)(A, B, C, m, k, n, stream=stream, **kw)
+
+
+def product_noalloc(op: int, A, B, C, m: int, k: int, n: int, stream=None) -> None:
+    """Cubic product that allocates nothing (fixed device scratch; see bmm.h)."""
+    _check(_lib_handle().bmm_product_noalloc(op, _ptr(A), _ptr(B), _ptr(C), m, k, n,
+                                             _stream(stream)), "bmm_product_noalloc")
 
 
 def workspace_size(op: int, m: int, k: int, n: int, **kw) -> int:

@@ -9,21 +9,29 @@
 // below 2^23). sm_103a has no 8-bit integer MMA (ptxas rejects
 // tcgen05.mma kind::i8 for this target), so FP8 is the exact tensor format.
 //
-// Persistent kernel, one CTA per SM, warp-specialised:
-//   warp 12     TMA producer: packed 128 x 128-bit tiles of A and 256 x
-//               128-bit tiles of Bt into a PSTAGES-deep shared ring
-//               (cp.async.bulk.tensor, mbarrier complete_tx).
-//   warps 0-7   expansion: each packed 32-bit word becomes 32 bytes of the
-//               K-major, no-swizzle canonical UMMA layout (8-row x 16-byte
-//               core matrices), into an ESTAGES-deep ring.
-//   warp 13     MMA issuer: 4 x tcgen05.mma (M=128, N=256, K=32) per stage
-//               into one of two TMEM accumulators (2 x 256 columns); commits
-//               release operand stages and publish finished accumulators.
-//   warps 8-11  epilogue: tcgen05.ld 32 lanes x 32 columns at a time, parity
-//               or non-zero test, bits repacked in registers (one row per
-//               thread) and stored as 64-bit words.
-// The two accumulators let the epilogue of one tile overlap the main loop of
-// the next; the same mechanism flushes long k in chunks (kchunk stages).
+// Persistent kernel, one CTA per SM, warp-specialised (22 warps):
+//   warp 20     TMA producer: packed tiles of 128 rows of A and 256 rows of
+//               Bt, 256 bits of k each (32-byte rows), into a PSTAGES-deep
+//               shared ring (cp.async.bulk.tensor, mbarrier complete_tx).
+//               Each packed stage feeds two operand stages of 128 bits.
+//   warps 8-15  A expansion: one row per thread, 256 bits -> 256 e4m3
+//               bytes (two operand stages) written straight into TMEM with
+//               tcgen05.st; two warps per TMEM lane quarter take alternate
+//               packed stages.
+//   warps 0-7   Bt expansion: each packed 32-bit word becomes 32 bytes of
+//               the K-major, 128-byte-swizzled canonical UMMA layout; a warp
+//               expands 4 whole rows of a packed stage at a time.
+//   warp 21     MMA issuer: per operand stage, one wait, 4 x tcgen05.mma
+//               (M=128, N=256, K=32; A from TMEM, B from shared memory) into
+//               the TMEM accumulator, one commit that frees the stage.
+//   warps 16-19 epilogue: tcgen05.ld 32 lanes x 32 columns at a time, parity
+//               or non-zero test, bits packed in registers with a shallow
+//               tree (one row per thread) and stored as 64-bit words.
+// The A and Bt halves of an operand stage share one "full" barrier (all
+// producers arrive) and one "empty" barrier (one commit). Keeping A in TMEM
+// means shared memory carries only Bt (written once, read once by the tensor
+// core). Long k is flushed from TMEM in chunks of `kchunk` stages (the
+// epilogue folds parities / ORs across chunks).
 //
 // Within every 32-element group of k the expansion permutes k (byte t of
 // output word j holds bit 8t + j of the packed word); A and Bt use the same
@@ -45,30 +53,37 @@ namespace {
 
 constexpr int BM = 128;          // rows of C per tile (UMMA M, TMEM lanes)
 constexpr int BN = 256;          // columns of C per tile (UMMA N)
-constexpr int KS = 128;          // k (bits) per stage
+constexpr int KS = 128;          // k (bits) per operand stage
+constexpr int KP = 256;          // k (bits) per packed (TMA) stage
+constexpr int SUB = KP / KS;     // operand stages per packed stage
 constexpr int MMA_K = 32;        // k per tcgen05.mma for 8-bit operands
-constexpr int PSTAGES = 6;       // packed ring depth
-constexpr int ESTAGES = 3;       // expanded ring depth
-constexpr int EXP_WARPS = 8;
-// warps 8..11: epilogue (warp % 4 = TMEM lane quarter)
-constexpr int TMA_WARP = 12;
-constexpr int MMA_WARP = 13;
-constexpr int THREADS = 14 * 32;
+constexpr int PSTAGES = 4;       // packed ring depth (shared)
+constexpr int ESTAGES = 4;       // operand ring depth (Bt in shared, A in TMEM)
+// 22 warps: an SM sub-partition (16 K registers) holds at most six of them,
+// which caps registers at 80 per thread.
+constexpr int BEXP_WARPS = 8;    // warps 0..7
+constexpr int AEXP_WARP0 = 8;    // warps 8..15: two per TMEM lane quarter, alternate stages
+constexpr int EPI_WARP0 = 16;    // warps 16..19 (warp % 4 = TMEM lane quarter)
+constexpr int TMA_WARP = 20;
+constexpr int MMA_WARP = 21;
+constexpr int THREADS = 22 * 32;
 constexpr int GROUP_M = 16;      // tile raster: 16 row-tiles per group
 
-constexpr int PA_BYTES = BM * KS / 8;    // 2 KB packed A per stage
-constexpr int PB_BYTES = BN * KS / 8;    // 4 KB packed Bt per stage
-constexpr int EA_BYTES = BM * KS;        // 16 KB expanded A per stage
-constexpr int EB_BYTES = BN * KS;        // 32 KB expanded Bt per stage
-constexpr int TMEM_COLS = 2 * BN;        // two fp32/s32 accumulators
+constexpr int PA_BYTES = BM * KP / 8;    // 4 KB packed A per packed stage
+constexpr int PB_BYTES = BN * KP / 8;    // 8 KB packed Bt per packed stage
+constexpr int EB_BYTES = BN * KS;        // 32 KB expanded Bt per operand stage
+constexpr int ACC_COL = 0;               // accumulator: TMEM columns [0, BN)
+constexpr int A_COL = BN;                // A ring: columns [BN, BN + ESTAGES * KS / 4)
+constexpr int A_STAGE_COLS = KS / 4;     // 4 e4m3 per 32-bit column
+constexpr int TMEM_COLS = 512;
+static_assert(A_COL + ESTAGES * A_STAGE_COLS <= TMEM_COLS, "TMEM budget");
 
-constexpr int OFF_EA = 0;
-constexpr int OFF_EB = OFF_EA + ESTAGES * EA_BYTES;
+constexpr int OFF_EB = 0;
 constexpr int OFF_PA = OFF_EB + ESTAGES * EB_BYTES;
 constexpr int OFF_PB = OFF_PA + PSTAGES * PA_BYTES;
 constexpr int OFF_BAR = OFF_PB + PSTAGES * PB_BYTES;
-// barriers: full_p[P], empty_p[P], full_e[E], empty_e[E], acc_full[2], acc_empty[2], drain
-constexpr int NBARS = 2 * PSTAGES + 2 * ESTAGES + 5;
+// barriers: full_p[P], empty_p[P], full_e[E], empty_e[E], acc_full, acc_empty, drain
+constexpr int NBARS = 2 * PSTAGES + 2 * ESTAGES + 3;
 constexpr int OFF_TMEM_SLOT = OFF_BAR + NBARS * 8;
 constexpr int SMEM_BYTES = OFF_TMEM_SLOT + 16 + 1024;  // + alignment slack
 
@@ -150,16 +165,20 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// Shared-memory matrix descriptor, no swizzle, K-major canonical layout:
-// LBO = byte distance between core matrices adjacent along K, SBO = between
-// core matrices adjacent along M/N (8-row groups).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor for a K-major operand in the 128-byte
+// swizzled canonical layout: each row's 128 bytes of k sit at row * 128,
+// 8-row groups form 1024-byte atoms (SBO = 1024 between them), and within an
+// atom the 16-byte chunk c of row r is stored at chunk c ^ (r % 8). The
+// start address may point k bytes into the first row (k < 128): the swizzle
+// is applied to absolute address bits, so atoms must be 1024-byte aligned.
+// Adding 2 to the descriptor advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-    // base offset 0, relative LBO mode, swizzle none (bits 61-63 = 0)
+    d |= (uint64_t)1 << 16;              // LBO: unused for swizzled K-major, 1 by convention
+    d |= (uint64_t)(1024u >> 4) << 32;   // SBO: 8-row atom stride
+    d |= (uint64_t)1 << 46;              // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;              // layout: 128-byte swizzle
     return d;
 }
 
@@ -169,13 +188,14 @@ __host__ __device__ constexpr uint32_t instr_desc(uint32_t dfmt) {
     return (dfmt << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
-                                       uint32_t accumulate) {
+// D (TMEM) += A (TMEM) x B (shared, descriptor).
+__device__ __forceinline__ void mma_f8_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t db,
+                                          uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(db), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -202,30 +222,60 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// ---------------------------------------------------------------- expansion
-// Packed word x holds 32 consecutive k of one row. Output word j (j = 0..7)
-// gets bit (8t + j) of x in byte t, moved to bit T of that byte:
-// T = 3 gives e4m3 0x08 = 2^-6, T = 0 gives u8 1.
-template <int T, int J>
-__device__ __forceinline__ uint32_t spread(uint32_t x) {
-    constexpr uint32_t mask = 0x01010101u << T;
-    if constexpr (T >= J)
-        return (x << (T - J)) & mask;
-    else
-        return (x >> (J - T)) & mask;
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(
+            taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+        "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]),
+        "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]),
+        "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
 }
 
-template <int T>
-__device__ __forceinline__ void expand_word(uint32_t x, uint32_t dst) {
-    const uint32_t y0 = spread<T, 0>(x), y1 = spread<T, 1>(x), y2 = spread<T, 2>(x),
-                   y3 = spread<T, 3>(x), y4 = spread<T, 4>(x), y5 = spread<T, 5>(x),
-                   y6 = spread<T, 6>(x), y7 = spread<T, 7>(x);
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(y0), "r"(y1), "r"(y2),
-                 "r"(y3)
-                 : "memory");
-    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst + 128), "r"(y4), "r"(y5),
-                 "r"(y6), "r"(y7)
-                 : "memory");
+// ---------------------------------------------------------------- expansion
+// Packed word x holds 32 consecutive k of one row. Output word j (j = 0..7)
+// gets bit (8t + j) of x in byte t, moved to bit 3 of that byte (e4m3 0x08 =
+// 2^-6). The moves are multiplications by powers of two (left) or high
+// halves of them (right) with factors the compiler cannot see, so they run
+// on the FMA pipe and leave the integer pipe the masks alone.
+struct Spread {
+    uint32_t f[8];  // f[j]: 2^(3-j) for j <= 3 (low product), 2^(35-j) for j > 3 (high)
+};
+
+__device__ __forceinline__ void spread8(uint32_t x, const Spread& sp, uint32_t* y) {
+    constexpr uint32_t mask = 0x08080808u;
+    y[0] = (x * sp.f[0]) & mask;
+    y[1] = (x * sp.f[1]) & mask;
+    y[2] = (x * sp.f[2]) & mask;
+    y[3] = x & mask;
+    y[4] = __umulhi(x, sp.f[4]) & mask;
+    y[5] = __umulhi(x, sp.f[5]) & mask;
+    y[6] = __umulhi(x, sp.f[6]) & mask;
+    y[7] = __umulhi(x, sp.f[7]) & mask;
+}
+
+// 32 result bits of one accumulator row slice -> one word, bit j from v[j].
+// GF(2): v[j] = count * 2^-12 exactly; adding 2^11 puts count's LSB in bit 0.
+// Boolean: any non-zero count. Packed with a 5-level tree of multiply-adds.
+template <int OP>
+__device__ __forceinline__ uint32_t pack_bits(const uint32_t (&v)[32]) {
+    uint32_t b[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+        if (OP == OP_GF2)
+            b[j] = __float_as_uint(__uint_as_float(v[j]) + 2048.0f) & 1u;
+        else
+            b[j] = min(v[j], 1u);  // fp32 counts are >= 0: non-zero bits <=> count > 0
+    }
+#pragma unroll
+    for (int w = 1; w < 32; w *= 2)
+#pragma unroll
+        for (int j = 0; j < 32; j += 2 * w) b[j] = b[j + w] * (1u << w) + b[j];
+    return b[0];
 }
 
 struct TileCoord {
@@ -250,9 +300,10 @@ __device__ __forceinline__ TileCoord tile_of(int t, int tiles_m, int tiles_n) {
 struct Params {
     uint64_t* C;
     int64_t ldc, strideC;
-    int m, n, nks, kchunk;  // kchunk: stages per accumulator flush
+    int m, n, nks, kchunk;  // nks operand stages per tile (even); kchunk: stages per flush
     int tiles_m, tiles_n, total_tiles;
     uint32_t* err;
+    Spread sp;
 };
 
 template <int OP>
@@ -267,9 +318,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     auto empty_p = [&](int s) { return bar0 + 8u * (PSTAGES + s); };
     auto full_e = [&](int s) { return bar0 + 8u * (2 * PSTAGES + s); };
     auto empty_e = [&](int s) { return bar0 + 8u * (2 * PSTAGES + ESTAGES + s); };
-    auto acc_full = [&](int b) { return bar0 + 8u * (2 * PSTAGES + 2 * ESTAGES + b); };
-    auto acc_empty = [&](int b) { return bar0 + 8u * (2 * PSTAGES + 2 * ESTAGES + 2 + b); };
-    const uint32_t drain_bar = bar0 + 8u * (2 * PSTAGES + 2 * ESTAGES + 4);
+    const uint32_t acc_full = bar0 + 8u * (2 * PSTAGES + 2 * ESTAGES);
+    const uint32_t acc_empty = acc_full + 8u;
+    const uint32_t drain_bar = acc_full + 16u;
     uint32_t* tmem_slot = (uint32_t*)(smem + OFF_TMEM_SLOT);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -277,16 +328,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < PSTAGES; s++) {
             mbar_init(full_p(s), 1);
-            mbar_init(empty_p(s), EXP_WARPS);
+            mbar_init(empty_p(s), BEXP_WARPS + 4);  // 8 Bt warps + the 4 A warps of that stage
         }
         for (int s = 0; s < ESTAGES; s++) {
-            mbar_init(full_e(s), EXP_WARPS);
+            mbar_init(full_e(s), BEXP_WARPS + 4);  // 8 Bt warps + the 4 A warps of that stage
             mbar_init(empty_e(s), 1);
         }
-        for (int b = 0; b < 2; b++) {
-            mbar_init(acc_full(b), 1);
-            mbar_init(acc_empty(b), 4);
-        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 4);
         mbar_init(drain_bar, 1);
         fence_barrier_init();
     }
@@ -310,113 +359,161 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     const int nks = p.nks;
     const int kchunk = p.kchunk;
+    int my_tiles = 0;
+    for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x) my_tiles++;
+    const int total_it = my_tiles * nks;  // operand stages this CTA runs
 
     if (warp == TMA_WARP) {
         // ---------------------------------------------------- TMA producer
         if (lane == 0) {
-            int it = 0;
+            int pit = 0;  // packed stages issued
             bool ok = true;
             for (int t = blockIdx.x; ok && t < p.total_tiles; t += gridDim.x) {
                 const TileCoord tc = tile_of(t, p.tiles_m, p.tiles_n);
-                for (int ks = 0; ks < nks; ks++, it++) {
-                    const int s = it % PSTAGES;
-                    if (!mbar_wait(empty_p(s), ((it / PSTAGES) & 1) ^ 1, p.err)) {
+                for (int kp = 0; kp < nks / SUB; kp++, pit++) {
+                    const int s = pit % PSTAGES;
+                    if (!mbar_wait(empty_p(s), ((pit / PSTAGES) & 1) ^ 1, p.err)) {
                         ok = false;
                         break;
                     }
                     mbar_arrive_tx(full_p(s), PA_BYTES + PB_BYTES);
-                    tma_load_3d(sbase + OFF_PA + s * PA_BYTES, &tmA, ks * (KS / 64), tc.tm * BM,
+                    tma_load_3d(sbase + OFF_PA + s * PA_BYTES, &tmA, kp * (KP / 64), tc.tm * BM,
                                 tc.leaf, full_p(s));
-                    tma_load_3d(sbase + OFF_PB + s * PB_BYTES, &tmB, ks * (KS / 64), tc.tn * BN,
+                    tma_load_3d(sbase + OFF_PB + s * PB_BYTES, &tmB, kp * (KP / 64), tc.tn * BN,
                                 tc.leaf, full_p(s));
                 }
             }
             // drain: the copies of the last issued stages must land before exit
-            for (int j = 1; j <= PSTAGES && j <= it; j++) {
-                const int i = it - j;
+            for (int j = 1; j <= PSTAGES && j <= pit; j++) {
+                const int i = pit - j;
                 if (!mbar_wait(full_p(i % PSTAGES), (i / PSTAGES) & 1, p.err)) break;
             }
         }
-    } else if (warp < EXP_WARPS) {
-        // ---------------------------------------------------- expansion
-        constexpr int TBIT = 3;  // e4m3 0x08
-        const int ri = lane & 7, wq = lane >> 3;
-        int it = 0;
-        bool ok = true;
-        for (int t = blockIdx.x; ok && t < p.total_tiles; t += gridDim.x) {
-            for (int ks = 0; ks < nks; ks++, it++) {
-                const int sp = it % PSTAGES, se = it % ESTAGES;
-                if (!mbar_wait(full_p(sp), (it / PSTAGES) & 1, p.err) ||
-                    !mbar_wait(empty_e(se), ((it / ESTAGES) & 1) ^ 1, p.err)) {
-                    ok = false;
-                    break;
-                }
-                const uint32_t pa = sbase + OFF_PA + sp * PA_BYTES;
-                const uint32_t pb = sbase + OFF_PB + sp * PB_BYTES;
-                const uint32_t ea = sbase + OFF_EA + se * EA_BYTES;
-                const uint32_t eb = sbase + OFF_EB + se * EB_BYTES;
-                // 48 row groups of 8 rows (16 of A, 32 of Bt); lane = (row in group, word)
+    } else if (warp < BEXP_WARPS) {
+        // ---------------------------------------------------- Bt expansion (shared)
+        // Per packed stage: 64 items of 4 rows x 8 packed words (both operand
+        // stages). Lane = (half h, row rr of the item, word wl of the half):
+        // word w = 4h + wl of the row goes to operand stage 2*pit + h. A
+        // quarter-warp then holds two adjacent rows (opposite parity) x 4 words
+        // of one half, whose swizzled 16-byte chunks are 8 distinct bank groups.
+        const int h = lane >> 4, rr = (lane >> 2) & 3, wl = lane & 3;
+        const Spread sp = p.sp;
+        const int total_pit = total_it / SUB;
+        static_assert(SUB == 2, "a packed stage feeds two operand stages");
+        for (int pit = 0; pit < total_pit; pit++) {
+            const int s = pit % PSTAGES;
+            const int it0 = pit * SUB;
+            const int se0 = it0 % ESTAGES, se1 = (it0 + 1) % ESTAGES;
+            if (!mbar_wait(full_p(s), (pit / PSTAGES) & 1, p.err) ||
+                !mbar_wait(empty_e(se0), ((it0 / ESTAGES) & 1) ^ 1, p.err) ||
+                !mbar_wait(empty_e(se1), (((it0 + 1) / ESTAGES) & 1) ^ 1, p.err))
+                break;
+            constexpr int ITEMS = (BN / 4) / BEXP_WARPS;
+            const uint32_t* pb = reinterpret_cast<const uint32_t*>(smem + OFF_PB + s * PB_BYTES);
+            uint8_t* eb = smem + OFF_EB + (h ? se1 : se0) * EB_BYTES;
+            uint32_t x[ITEMS];
 #pragma unroll
-                for (int q = 0; q < 6; q++) {
-                    const int g = warp + EXP_WARPS * q;
-                    uint32_t src, dst;
-                    if (g < BM / 8) {
-                        src = pa + (g * 8 + ri) * (KS / 8) + wq * 4;
-                        dst = ea + g * 1024 + (2 * wq) * 128 + ri * 16;
-                    } else {
-                        const int gb = g - BM / 8;
-                        src = pb + (gb * 8 + ri) * (KS / 8) + wq * 4;
-                        dst = eb + gb * 1024 + (2 * wq) * 128 + ri * 16;
-                    }
-                    uint32_t x;
-                    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(x) : "r"(src) : "memory");
-                    expand_word<TBIT>(x, dst);
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(empty_p(sp));
-                fence_proxy_async();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(full_e(se));
+            for (int q = 0; q < ITEMS; q++)
+                x[q] = pb[((warp + BEXP_WARPS * q) * 4 + rr) * 8 + 4 * h + wl];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty_p(s));
+#pragma unroll
+            for (int q = 0; q < ITEMS; q++) {
+                const int row = (warp + BEXP_WARPS * q) * 4 + rr;
+                uint8_t* rowp = eb + row * 128;
+                uint32_t y[8];
+                spread8(x[q], sp, y);
+                *reinterpret_cast<uint4*>(rowp + (((2 * wl) ^ (row & 7)) * 16)) =
+                    make_uint4(y[0], y[1], y[2], y[3]);
+                *reinterpret_cast<uint4*>(rowp + (((2 * wl + 1) ^ (row & 7)) * 16)) =
+                    make_uint4(y[4], y[5], y[6], y[7]);
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(full_e(se0));
+                mbar_arrive(full_e(se1));
+            }
+        }
+    } else if (warp < EPI_WARP0) {
+        // ---------------------------------------------------- A expansion (TMEM)
+        const int quarter = warp & 3;
+        const int parity = (warp - AEXP_WARP0) >> 2;  // this warp takes packed stages pit % 2 == parity
+        const int row = 32 * quarter + lane;
+        const Spread sp = p.sp;
+        const uint32_t tlane = (uint32_t)(32 * quarter) << 16;
+        const int total_pit = total_it / SUB;
+        for (int pit = parity; pit < total_pit; pit += 2) {
+            const int s = pit % PSTAGES;
+            const int it0 = pit * SUB;
+            const int se0 = it0 % ESTAGES, se1 = (it0 + 1) % ESTAGES;
+            if (!mbar_wait(full_p(s), (pit / PSTAGES) & 1, p.err))
+                break;
+            const uint4* src = reinterpret_cast<const uint4*>(smem + OFF_PA + s * PA_BYTES +
+                                                              row * (KP / 8));
+            const uint4 xa = src[0], xb = src[1];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty_p(s));
+            uint32_t y[32];
+            if (!mbar_wait(empty_e(se0), ((it0 / ESTAGES) & 1) ^ 1, p.err)) break;
+            spread8(xa.x, sp, y);
+            spread8(xa.y, sp, y + 8);
+            spread8(xa.z, sp, y + 16);
+            spread8(xa.w, sp, y + 24);
+            tmem_st32(tmem + tlane + (uint32_t)(A_COL + se0 * A_STAGE_COLS), y);
+            if (!mbar_wait(empty_e(se1), (((it0 + 1) / ESTAGES) & 1) ^ 1, p.err)) break;
+            spread8(xb.x, sp, y);
+            spread8(xb.y, sp, y + 8);
+            spread8(xb.z, sp, y + 16);
+            spread8(xb.w, sp, y + 24);
+            tmem_st32(tmem + tlane + (uint32_t)(A_COL + se1 * A_STAGE_COLS), y);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(full_e(se0));
+                mbar_arrive(full_e(se1));
             }
         }
     } else if (warp == MMA_WARP) {
         // ---------------------------------------------------- MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = instr_desc(1u);
-            int it = 0, seg = 0;
+            uint64_t db0[ESTAGES];
+#pragma unroll
+            for (int s = 0; s < ESTAGES; s++) db0[s] = smem_desc_sw128(sbase + OFF_EB + s * EB_BYTES);
+            int seg = 0, kin = 0, ks = 0;
             bool ok = true;
-            for (int t = blockIdx.x; ok && t < p.total_tiles; t += gridDim.x) {
-                int b = 0;
-                for (int ks = 0; ks < nks; ks++, it++) {
-                    const int kin = ks % kchunk;
-                    if (kin == 0) {
-                        b = seg & 1;
-                        if (!mbar_wait(acc_empty(b), ((seg >> 1) & 1) ^ 1, p.err)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                    }
-                    const int se = it % ESTAGES;
-                    if (!mbar_wait(full_e(se), (it / ESTAGES) & 1, p.err)) {
+            for (int it = 0; it < total_it; it++) {
+                if (kin == 0) {
+                    if (!mbar_wait(acc_empty, (seg & 1) ^ 1, p.err)) {
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
-                    const uint32_t ea = sbase + OFF_EA + se * EA_BYTES;
-                    const uint32_t eb = sbase + OFF_EB + se * EB_BYTES;
+                }
+                const int se = it % ESTAGES;
+                if (!mbar_wait(full_e(se), (it / ESTAGES) & 1, p.err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t ta = tmem + (uint32_t)(A_COL + se * A_STAGE_COLS);
+                uint64_t db = db0[0];
 #pragma unroll
-                    for (int j = 0; j < KS / MMA_K; j++) {
-                        const uint64_t da = smem_desc(ea + j * 256, 128, 1024);
-                        const uint64_t db = smem_desc(eb + j * 256, 128, 1024);
-                        mma_f8(tmem + (uint32_t)(b * BN), da, db, idesc,
-                               (kin > 0 || j > 0) ? 1u : 0u);
-                    }
-                    mma_commit(empty_e(se));
-                    if (kin == kchunk - 1 || ks == nks - 1) {
-                        mma_commit(acc_full(b));
-                        seg++;
-                    }
+                for (int s = 1; s < ESTAGES; s++)
+                    if (se == s) db = db0[s];
+#pragma unroll
+                for (int j = 0; j < KS / MMA_K; j++)
+                    mma_f8_ta(tmem + ACC_COL, ta + j * (MMA_K / 4), db + 2 * j, idesc,
+                              (kin > 0 || j > 0) ? 1u : 0u);
+                mma_commit(empty_e(se));
+                kin++;
+                ks++;
+                if (kin == kchunk || ks == nks) {
+                    mma_commit(acc_full);
+                    seg++;
+                    kin = 0;
+                    if (ks == nks) ks = 0;
                 }
             }
             if (!ok) {  // wait (bounded) for every MMA this thread issued
@@ -424,9 +521,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                 mbar_wait(drain_bar, 0, p.err);
             }
         }
-    } else {
+    } else if (warp < TMA_WARP) {
         // ---------------------------------------------------- epilogue
         const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+        const uint32_t tlane = (uint32_t)(32 * quarter) << 16;
         const int nseg = (nks + kchunk - 1) / kchunk;
         int seg = 0;
         bool ok = true;
@@ -436,27 +534,16 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int c = 0; c < BN / 32; c++) words[c] = 0u;
             for (int g = 0; g < nseg; g++, seg++) {
-                const int b = seg & 1;
-                if (!mbar_wait(acc_full(b), (seg >> 1) & 1, p.err)) {
+                if (!mbar_wait(acc_full, seg & 1, p.err)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-#pragma unroll
+#pragma unroll 2
                 for (int c = 0; c < BN / 32; c++) {
                     uint32_t v[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * BN + 32 * c),
-                              v);
-                    uint32_t wbits = 0;
-#pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        // value = count * 2^-12, exact; + 2^11 puts count's LSB in bit 0
-                        const uint32_t bit =
-                            (OP == OP_GF2)
-                                ? (__float_as_uint(__uint_as_float(v[j]) + 2048.0f) & 1u)
-                                : (v[j] != 0u ? 1u : 0u);
-                        wbits |= bit << j;
-                    }
+                    tmem_ld32(tmem + tlane + (uint32_t)(ACC_COL + 32 * c), v);
+                    const uint32_t wbits = pack_bits<OP>(v);
                     if (OP == OP_GF2)
                         words[c] ^= wbits;
                     else
@@ -464,7 +551,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(acc_empty(b));
+                if (lane == 0) mbar_arrive(acc_empty);
             }
             if (!ok) break;
             const int64_t row = (int64_t)tc.tm * BM + 32 * quarter + lane;
@@ -505,7 +592,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 3-D map over uint64 words: (k/64 words, rows, leaves), box (KS/64, box_rows, 1).
+// 3-D map over uint64 words: (k/64 words, rows, leaves), box (KP/64, box_rows, 1).
+// Boxes that run past k or the rows are zero-filled, which adds nothing to
+// the counts.
 bool make_map(CUtensorMap* map, const uint64_t* base, int64_t kwords, int64_t rows,
               int64_t pitch, int64_t count, int64_t stride, int box_rows) {
     auto fn = encode_fn();
@@ -513,7 +602,7 @@ bool make_map(CUtensorMap* map, const uint64_t* base, int64_t kwords, int64_t ro
     cuuint64_t dims[3] = {(cuuint64_t)kwords, (cuuint64_t)rows, (cuuint64_t)count};
     const int64_t leaf_stride = count > 1 ? stride : rows * pitch;
     cuuint64_t strides[2] = {(cuuint64_t)(pitch * 8), (cuuint64_t)(leaf_stride * 8)};
-    cuuint32_t box[3] = {(cuuint32_t)(KS / 64), (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)(KP / 64), (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void*)base, dims, strides, box,
                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -569,7 +658,7 @@ bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int6
     prm.strideC = strideC;
     prm.m = (int)m;
     prm.n = (int)n;
-    prm.nks = (int)(k / KS);
+    prm.nks = (int)((k + KP - 1) / KP) * SUB;  // whole packed stages; the tail is zero-filled
     prm.kchunk = tc_kchunk_stages(path, prm.nks);
     prm.tiles_m = (int)((m + BM - 1) / BM);
     prm.tiles_n = (int)((n + BN - 1) / BN);
@@ -577,6 +666,7 @@ bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int6
     if (total > 0x7fffffff) return BMM_ERR_UNSUPPORTED;
     prm.total_tiles = (int)total;
     prm.err = err;
+    for (int j = 0; j < 8; j++) prm.sp.f[j] = j <= 3 ? (1u << (3 - j)) : (1u << (35 - j));
     TraceScope ts(BMM_PHASE_BASE, s);
     const cudaError_t e =
         (op == OP_GF2) ? launch_tc<OP_GF2>(ma, mb, prm, s) : launch_tc<OP_BOOL>(ma, mb, prm, s);

@@ -21,14 +21,19 @@
 //   warps 0-7   Bt expansion: each packed 32-bit word becomes 32 bytes of
 //               the K-major, 128-byte-swizzled canonical UMMA layout; a warp
 //               expands 4 whole rows of a packed stage at a time.
-//   warp 21     MMA issuer: per operand stage, one wait, 4 x tcgen05.mma
-//               (M=128, N=256, K=32; A from TMEM, B from shared memory) into
-//               the TMEM accumulator, one commit that frees the stage.
+//   warp 21     MMA issuer: per packed stage, one wait, then for each of its
+//               two operand stages 4 x tcgen05.mma (M=128, N=256, K=32; A
+//               from TMEM, B from shared memory) into the TMEM accumulator
+//               and one commit that frees that operand stage.
 //   warps 16-19 epilogue: tcgen05.ld 32 lanes x 32 columns at a time, parity
 //               or non-zero test, bits packed in registers with a shallow
 //               tree (one row per thread) and stored as 64-bit words.
 // The A and Bt halves of an operand stage share one "full" barrier (all
-// producers arrive) and one "empty" barrier (one commit). Keeping A in TMEM
+// producers arrive) and one "empty" barrier (one commit). Every producer
+// arrives on the first operand stage of a packed stage before the second,
+// and commits complete in order, so waiting for the second stage's barrier
+// covers both: each role checks one barrier per packed stage (a check costs
+// ~190 cycles of latency, even when the phase is already complete). Keeping A in TMEM
 // means shared memory carries only Bt (written once, read once by the tensor
 // core). Long k is flushed from TMEM in chunks of `kchunk` stages (the
 // epilogue folds parities / ORs across chunks).
@@ -405,7 +410,6 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int it0 = pit * SUB;
             const int se0 = it0 % ESTAGES, se1 = (it0 + 1) % ESTAGES;
             if (!mbar_wait(full_p(s), (pit / PSTAGES) & 1, p.err) ||
-                !mbar_wait(empty_e(se0), ((it0 / ESTAGES) & 1) ^ 1, p.err) ||
                 !mbar_wait(empty_e(se1), (((it0 + 1) / ESTAGES) & 1) ^ 1, p.err))
                 break;
             constexpr int ITEMS = (BN / 4) / BEXP_WARPS;
@@ -455,13 +459,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(empty_p(s));
             uint32_t y[32];
-            if (!mbar_wait(empty_e(se0), ((it0 / ESTAGES) & 1) ^ 1, p.err)) break;
+            if (!mbar_wait(empty_e(se1), (((it0 + 1) / ESTAGES) & 1) ^ 1, p.err)) break;
             spread8(xa.x, sp, y);
             spread8(xa.y, sp, y + 8);
             spread8(xa.z, sp, y + 16);
             spread8(xa.w, sp, y + 24);
             tmem_st32(tmem + tlane + (uint32_t)(A_COL + se0 * A_STAGE_COLS), y);
-            if (!mbar_wait(empty_e(se1), (((it0 + 1) / ESTAGES) & 1) ^ 1, p.err)) break;
             spread8(xb.x, sp, y);
             spread8(xb.y, sp, y + 8);
             spread8(xb.z, sp, y + 16);
@@ -484,32 +487,37 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int s = 0; s < ESTAGES; s++) db0[s] = smem_desc_sw128(sbase + OFF_EB + s * EB_BYTES);
             int seg = 0, kin = 0, ks = 0;
             bool ok = true;
-            for (int it = 0; it < total_it; it++) {
+            const int total_pit = total_it / SUB;
+            for (int pit = 0; pit < total_pit; pit++) {
                 if (kin == 0) {
                     if (!mbar_wait(acc_empty, (seg & 1) ^ 1, p.err)) {
                         ok = false;
                         break;
                     }
                 }
-                const int se = it % ESTAGES;
-                if (!mbar_wait(full_e(se), (it / ESTAGES) & 1, p.err)) {
+                const int it0 = pit * SUB;
+                if (!mbar_wait(full_e((it0 + 1) % ESTAGES), ((it0 + 1) / ESTAGES) & 1, p.err)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t ta = tmem + (uint32_t)(A_COL + se * A_STAGE_COLS);
-                uint64_t db = db0[0];
 #pragma unroll
-                for (int s = 1; s < ESTAGES; s++)
-                    if (se == s) db = db0[s];
+                for (int sub = 0; sub < SUB; sub++) {
+                    const int se = (it0 + sub) % ESTAGES;
+                    const uint32_t ta = tmem + (uint32_t)(A_COL + se * A_STAGE_COLS);
+                    uint64_t db = db0[0];
 #pragma unroll
-                for (int j = 0; j < KS / MMA_K; j++)
-                    mma_f8_ta(tmem + ACC_COL, ta + j * (MMA_K / 4), db + 2 * j, idesc,
-                              (kin > 0 || j > 0) ? 1u : 0u);
-                mma_commit(empty_e(se));
-                kin++;
-                ks++;
-                if (kin == kchunk || ks == nks) {
+                    for (int s = 1; s < ESTAGES; s++)
+                        if (se == s) db = db0[s];
+#pragma unroll
+                    for (int j = 0; j < KS / MMA_K; j++)
+                        mma_f8_ta(tmem + ACC_COL, ta + j * (MMA_K / 4), db + 2 * j, idesc,
+                                  (kin > 0 || sub > 0 || j > 0) ? 1u : 0u);
+                    mma_commit(empty_e(se));
+                }
+                kin += SUB;
+                ks += SUB;
+                if (kin >= kchunk || ks == nks) {
                     mma_commit(acc_full);
                     seg++;
                     kin = 0;
@@ -632,9 +640,11 @@ bool tc_path_available() { return device_cc() == 103 && encode_fn() != nullptr; 
 
 // Longest run of k stages accumulated before the counts are flushed from
 // TMEM: the e4m3 path reads parity through an FP32 value count * 2^-12,
-// exact while count < 2^23 (at most 65535 stages of 128); S32 needs none.
+// exact while count < 2^23 (at most 65534 stages of 128); S32 needs none.
 int tc_kchunk_stages(int path, int nks) {
-    if (path == BMM_PATH_TC_FP8) return nks < 65535 ? nks : 65535;
+    // a multiple of the operand stages per packed stage (flushes happen between packed stages)
+    const int cap = 65534;
+    if (path == BMM_PATH_TC_FP8) return nks < cap ? nks : cap;
     return nks;
 }
 

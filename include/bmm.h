@@ -115,15 +115,36 @@ typedef struct {
 bmm_status bmm_plan(int32_t op, int64_t m, int64_t k, int64_t n, const bmm_opts *opts,
                     bmm_plan_info *info);
 
-/* Batched independent products C_i = A_i B_i, i < count, of individual sizes,
- * in one persistent launch. The pointer and size arrays are HOST memory; the
- * matrices are device memory as above. op: 0 binary (cubic), 1 Boolean. */
+/* Batched independent products C_i = A_i B_i, i < count, of individual sizes
+ * (each a multiple of 64), all in one persistent launch of the base case.
+ * op[i]: 0 binary, 1 Boolean (cubic; the batch may mix them). The pointer
+ * and size arrays are HOST memory; the matrices are device memory as above.
+ * These one-shot forms build a plan, run it on `stream` and wait for the
+ * stream before freeing the plan, so they return with the products done. */
+bmm_status bmm_batched(int32_t count, const int32_t *op, const uint64_t *const *A,
+                       const uint64_t *const *B, uint64_t *const *C, const int64_t *m,
+                       const int64_t *k, const int64_t *n, bmm_stream_t stream);
 bmm_status bmm_gf2_batched(int32_t count, const uint64_t *const *A, const uint64_t *const *B,
                            uint64_t *const *C, const int64_t *m, const int64_t *k,
                            const int64_t *n, bmm_stream_t stream);
 bmm_status bmm_bool_batched(int32_t count, const uint64_t *const *A, const uint64_t *const *B,
                             uint64_t *const *C, const int64_t *m, const int64_t *k,
                             const int64_t *n, bmm_stream_t stream);
+
+/* Reusable batch plan. create builds, on the current device: TMA maps per
+ * problem, the tile work list and its assignment to SMs (longest first onto
+ * the least loaded SM), and scratch for the transposed B's; it allocates
+ * device memory and copies to it synchronously. run launches three kernels on
+ * `stream` (batched transpose, row padding for k/64 odd, persistent base
+ * case), allocates nothing and does not synchronise; it reads the matrices
+ * named at create time, so new data in the same buffers needs no new plan.
+ * destroy frees the plan; call it only after the runs have completed. */
+typedef struct bmm_batched_plan_s *bmm_batched_plan;
+bmm_status bmm_batched_plan_create(int32_t count, const int32_t *op, const uint64_t *const *A,
+                                   const uint64_t *const *B, uint64_t *const *C, const int64_t *m,
+                                   const int64_t *k, const int64_t *n, bmm_batched_plan *plan);
+bmm_status bmm_batched_plan_run(bmm_batched_plan plan, bmm_stream_t stream);
+bmm_status bmm_batched_plan_destroy(bmm_batched_plan plan);
 
 /* ---- the steps of the path, exported for tests and experiments ---------- */
 

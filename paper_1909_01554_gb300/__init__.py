@@ -23,7 +23,8 @@ GF2, BOOL = 0, 1
 
 EXPORTED = [
     "bmm_opts_default", "bmm_gf2", "bmm_bool", "bmm_gf2_ex", "bmm_bool_ex", "bmm_workspace_size",
-    "bmm_gf2_batched", "bmm_bool_batched", "bmm_transpose", "bmm_base_product",
+    "bmm_gf2_batched", "bmm_bool_batched", "bmm_batched", "bmm_batched_plan_create",
+    "bmm_batched_plan_run", "bmm_batched_plan_destroy", "bmm_transpose", "bmm_base_product",
     "bmm_basis_change", "bmm_stream_status", "bmm_status_string", "bmm_last_cuda_error",
     "bmm_device_supported", "bmm_plan", "bmm_product_noalloc", "bmm_trace_enable", "bmm_trace_read", "bmm_launch_count",
 ]
@@ -76,6 +77,15 @@ def _lib_handle():
         for f in (L.bmm_gf2_batched, L.bmm_bool_batched):
             f.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp]
             f.restype = i32
+        L.bmm_batched.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.bmm_batched.restype = i32
+        L.bmm_batched_plan_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp,
+                                              ctypes.POINTER(ctypes.c_void_p)]
+        L.bmm_batched_plan_create.restype = i32
+        L.bmm_batched_plan_run.argtypes = [vp, vp]
+        L.bmm_batched_plan_run.restype = i32
+        L.bmm_batched_plan_destroy.argtypes = [vp]
+        L.bmm_batched_plan_destroy.restype = i32
         L.bmm_transpose.argtypes = [vp, vp, i64, i64, vp]
         L.bmm_transpose.restype = i32
         L.bmm_base_product.argtypes = [i32, i32, vp, vp, vp, i64, i64, i64, vp]
@@ -218,15 +228,50 @@ def basis_change(variant: int, inverse: bool, X, rows: int, cols: int, depth: in
                                           _stream(stream)), "bmm_basis_change")
 
 
-def batched(op: int, As, Bs, Cs, ms, ks, ns, stream=None) -> None:
-    """C_i = A_i B_i for every i, in one persistent launch (host pointer arrays)."""
+def _batch_arrays(ops, As, Bs, Cs, ms, ks, ns):
     count = len(As)
     P = ctypes.c_void_p * count
     I = ctypes.c_int64 * count
-    a, b, c = P(*map(_ptr, As)), P(*map(_ptr, Bs)), P(*map(_ptr, Cs))
-    mm, kk, nn = I(*ms), I(*ks), I(*ns)
-    f = _lib_handle().bmm_gf2_batched if op == GF2 else _lib_handle().bmm_bool_batched
-    _check(f(count, a, b, c, mm, kk, nn, _stream(stream)), "bmm_batched")
+    O = ctypes.c_int32 * count
+    return (count, O(*ops), P(*map(_ptr, As)), P(*map(_ptr, Bs)), P(*map(_ptr, Cs)), I(*ms),
+            I(*ks), I(*ns))
+
+
+def batched(ops, As, Bs, Cs, ms, ks, ns, stream=None) -> None:
+    """C_i = A_i B_i for every i in one persistent launch; ops[i] 0 = GF(2),
+    1 = Boolean (or one int for the whole batch). Returns when done."""
+    if isinstance(ops, int):
+        ops = [ops] * len(As)
+    arr = _batch_arrays(ops, As, Bs, Cs, ms, ks, ns)
+    _check(_lib_handle().bmm_batched(*arr, _stream(stream)), "bmm_batched")
+
+
+class BatchedPlan:
+    """A reusable batch plan (see bmm_batched_plan_create); run() only launches."""
+
+    def __init__(self, ops, As, Bs, Cs, ms, ks, ns):
+        if isinstance(ops, int):
+            ops = [ops] * len(As)
+        self._arr = _batch_arrays(ops, As, Bs, Cs, ms, ks, ns)
+        h = ctypes.c_void_p(0)
+        _check(_lib_handle().bmm_batched_plan_create(*self._arr, ctypes.byref(h)),
+               "bmm_batched_plan_create")
+        self._h = h
+
+    def run(self, stream=None) -> None:
+        _check(_lib_handle().bmm_batched_plan_run(self._h, _stream(stream)),
+               "bmm_batched_plan_run")
+
+    def destroy(self) -> None:
+        if self._h:
+            _check(_lib_handle().bmm_batched_plan_destroy(self._h), "bmm_batched_plan_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def stream_status(stream=None) -> None:

@@ -48,6 +48,18 @@ cudaError_t launch_transpose_pitched(const uint64_t* X, int64_t pitch, uint64_t*
                                      int64_t tpitch, int64_t rows, int64_t cols,
                                      cudaStream_t s);
 
+// One transpose of a batch: Xt (cols x rows, pitch tpitch) = X^T (rows x cols, pitch pitch).
+struct TransposeJob {
+    const uint64_t* X;
+    uint64_t* Xt;
+    int64_t pitch, tpitch, rows, cols;
+};
+// CTA tiles one transpose takes (the batched launch needs their prefix sums).
+int64_t transpose_tiles(int64_t rows, int64_t cols);
+// All jobs in one launch; first[i] = tiles of jobs 0..i-1 (device arrays).
+cudaError_t launch_transpose_batched(const TransposeJob* jobs, const int64_t* first, int count,
+                                     int64_t total_tiles, cudaStream_t s);
+
 // CUDA-core base case: C (m x n, row pitch ldc words) = A (m x k, pitch lda)
 // times Bt^T (Bt n x k, pitch ldb), GF(2) or Boolean.
 // Leaf h of a batch of `count` starts at A + h*strideA, Bt + h*strideB,

@@ -1,0 +1,41 @@
+// Descriptors shared by the batched form of the tensor-core base case and
+// the host code that plans it.
+#pragma once
+
+#include <cuda.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace bmm {
+
+// One product of the batch, as the persistent kernel sees it (global memory,
+// 64-byte aligned so the TMA maps inside can be used in place).
+struct alignas(64) TcProblem {
+    CUtensorMap mapA;  // A (m x k), 3-D map (k words, m rows, 1)
+    CUtensorMap mapB;  // Bt (n x k)
+    uint64_t* C;
+    int64_t ldc;       // words
+    int32_t m, n, nks, op;  // nks: 128-bit k stages, a multiple of 2
+};
+
+// One output tile (128 rows x 256 columns) of one problem.
+struct TcWorkItem {
+    int32_t prob, tm, tn, cost;
+};
+
+constexpr int TC_TILE_M = 128;
+constexpr int TC_TILE_N = 256;
+constexpr int TC_PACKED_BITS = 256;  // k granularity of the TMA stages
+
+// Fills the host copy of a problem descriptor (TMA maps need k % 128 == 0
+// and even pitches). Returns false if a map cannot be encoded.
+bool tc_make_problem(TcProblem* out, const uint64_t* A, int64_t lda, const uint64_t* Bt,
+                     int64_t ldb, uint64_t* C, int64_t ldc, int64_t m, int64_t k, int64_t n,
+                     int op);
+
+// One persistent launch over the per-CTA work lists (cta_ptr has grid + 1 entries).
+cudaError_t tc_launch_batched(const TcProblem* d_probs, const TcWorkItem* d_items,
+                              const int32_t* d_cta_ptr, int grid, cudaStream_t s);
+
+}  // namespace bmm

@@ -49,17 +49,19 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "plan.h"
+#include "tc_batched.h"
 
 namespace bmm {
 namespace {
 
-constexpr int BM = 128;          // rows of C per tile (UMMA M, TMEM lanes)
-constexpr int BN = 256;          // columns of C per tile (UMMA N)
+constexpr int BM = TC_TILE_M;    // rows of C per tile (UMMA M, TMEM lanes)
+constexpr int BN = TC_TILE_N;    // columns of C per tile (UMMA N)
 constexpr int KS = 128;          // k (bits) per operand stage
-constexpr int KP = 256;          // k (bits) per packed (TMA) stage
+constexpr int KP = TC_PACKED_BITS;  // k (bits) per packed (TMA) stage
 constexpr int SUB = KP / KS;     // operand stages per packed stage
 constexpr int MMA_K = 32;        // k per tcgen05.mma for 8-bit operands
 constexpr int PSTAGES = 4;       // packed ring depth (shared)
@@ -303,15 +305,79 @@ __device__ __forceinline__ TileCoord tile_of(int t, int tiles_m, int tiles_n) {
 }
 
 struct Params {
+    // uniform form: one shape, `count` leaves side by side
     uint64_t* C;
     int64_t ldc, strideC;
-    int m, n, nks, kchunk;  // nks operand stages per tile (even); kchunk: stages per flush
+    int m, n, nks, op;
     int tiles_m, tiles_n, total_tiles;
+    // batched form: per-problem descriptors and per-CTA work lists
+    const TcProblem* probs;
+    const TcWorkItem* items;
+    const int32_t* cta_ptr;
+    int kchunk;  // stages per flush (both forms)
     uint32_t* err;
     Spread sp;
 };
 
-template <int OP>
+// Everything a role needs about one output tile.
+struct Tile {
+    const CUtensorMap* ma;
+    const CUtensorMap* mb;
+    uint64_t* C;  // leaf's C
+    int64_t ldc;
+    int m, n, nks, op, tm, tn, leaf;
+};
+
+template <bool BATCHED>
+__device__ __forceinline__ int tile_count(const Params& p) {
+    if (BATCHED) return p.cta_ptr[blockIdx.x + 1] - p.cta_ptr[blockIdx.x];
+    int c = 0;
+    for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x) c++;
+    return c;
+}
+
+template <bool BATCHED>
+__device__ __forceinline__ Tile tile_get(const Params& p, int idx, const CUtensorMap* tmA,
+                                         const CUtensorMap* tmB) {
+    Tile t;
+    if (BATCHED) {
+        const TcWorkItem w = p.items[p.cta_ptr[blockIdx.x] + idx];
+        const TcProblem* d = p.probs + w.prob;
+        t.ma = &d->mapA;
+        t.mb = &d->mapB;
+        t.C = d->C;
+        t.ldc = d->ldc;
+        t.m = d->m;
+        t.n = d->n;
+        t.nks = d->nks;
+        t.op = d->op;
+        t.tm = w.tm;
+        t.tn = w.tn;
+        t.leaf = 0;
+    } else {
+        const TileCoord c = tile_of(blockIdx.x + idx * gridDim.x, p.tiles_m, p.tiles_n);
+        t.ma = tmA;
+        t.mb = tmB;
+        t.C = p.C + (int64_t)c.leaf * p.strideC;
+        t.ldc = p.ldc;
+        t.m = p.m;
+        t.n = p.n;
+        t.nks = p.nks;
+        t.op = p.op;
+        t.tm = c.tm;
+        t.tn = c.tn;
+        t.leaf = c.leaf;
+    }
+    return t;
+}
+
+template <bool BATCHED>
+__device__ __forceinline__ int tile_nks(const Params& p, int idx) {
+    if (BATCHED) return p.probs[p.items[p.cta_ptr[blockIdx.x] + idx].prob].nks;
+    return p.nks;
+}
+
+template <bool BATCHED>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const Params p) {
@@ -351,7 +417,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (warp == TMA_WARP && lane == 0) {
+    if (!BATCHED && warp == TMA_WARP && lane == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA))
                      : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB))
@@ -362,29 +428,28 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int nks = p.nks;
     const int kchunk = p.kchunk;
-    int my_tiles = 0;
-    for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x) my_tiles++;
-    const int total_it = my_tiles * nks;  // operand stages this CTA runs
+    const int my_tiles = tile_count<BATCHED>(p);
+    int total_it = 0;  // operand stages this CTA runs
+    for (int i = 0; i < my_tiles; i++) total_it += tile_nks<BATCHED>(p, i);
 
     if (warp == TMA_WARP) {
         // ---------------------------------------------------- TMA producer
         if (lane == 0) {
             int pit = 0;  // packed stages issued
             bool ok = true;
-            for (int t = blockIdx.x; ok && t < p.total_tiles; t += gridDim.x) {
-                const TileCoord tc = tile_of(t, p.tiles_m, p.tiles_n);
-                for (int kp = 0; kp < nks / SUB; kp++, pit++) {
+            for (int i = 0; ok && i < my_tiles; i++) {
+                const Tile tc = tile_get<BATCHED>(p, i, &tmA, &tmB);
+                for (int kp = 0; kp < tc.nks / SUB; kp++, pit++) {
                     const int s = pit % PSTAGES;
                     if (!mbar_wait(empty_p(s), ((pit / PSTAGES) & 1) ^ 1, p.err)) {
                         ok = false;
                         break;
                     }
                     mbar_arrive_tx(full_p(s), PA_BYTES + PB_BYTES);
-                    tma_load_3d(sbase + OFF_PA + s * PA_BYTES, &tmA, kp * (KP / 64), tc.tm * BM,
+                    tma_load_3d(sbase + OFF_PA + s * PA_BYTES, tc.ma, kp * (KP / 64), tc.tm * BM,
                                 tc.leaf, full_p(s));
-                    tma_load_3d(sbase + OFF_PB + s * PB_BYTES, &tmB, kp * (KP / 64), tc.tn * BN,
+                    tma_load_3d(sbase + OFF_PB + s * PB_BYTES, tc.mb, kp * (KP / 64), tc.tn * BN,
                                 tc.leaf, full_p(s));
                 }
             }
@@ -485,43 +550,44 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint64_t db0[ESTAGES];
 #pragma unroll
             for (int s = 0; s < ESTAGES; s++) db0[s] = smem_desc_sw128(sbase + OFF_EB + s * EB_BYTES);
-            int seg = 0, kin = 0, ks = 0;
+            int seg = 0, pit = 0;
             bool ok = true;
-            const int total_pit = total_it / SUB;
-            for (int pit = 0; pit < total_pit; pit++) {
-                if (kin == 0) {
-                    if (!mbar_wait(acc_empty, (seg & 1) ^ 1, p.err)) {
+            for (int i = 0; ok && i < my_tiles; i++) {
+                const int nks = tile_nks<BATCHED>(p, i);
+                int kin = 0;
+                for (int ks = 0; ks < nks; ks += SUB, pit++) {
+                    if (kin == 0) {
+                        if (!mbar_wait(acc_empty, (seg & 1) ^ 1, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    const int it0 = pit * SUB;
+                    if (!mbar_wait(full_e((it0 + 1) % ESTAGES), ((it0 + 1) / ESTAGES) & 1, p.err)) {
                         ok = false;
                         break;
                     }
-                }
-                const int it0 = pit * SUB;
-                if (!mbar_wait(full_e((it0 + 1) % ESTAGES), ((it0 + 1) / ESTAGES) & 1, p.err)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
+                    tc_fence_after();
 #pragma unroll
-                for (int sub = 0; sub < SUB; sub++) {
-                    const int se = (it0 + sub) % ESTAGES;
-                    const uint32_t ta = tmem + (uint32_t)(A_COL + se * A_STAGE_COLS);
-                    uint64_t db = db0[0];
+                    for (int sub = 0; sub < SUB; sub++) {
+                        const int se = (it0 + sub) % ESTAGES;
+                        const uint32_t ta = tmem + (uint32_t)(A_COL + se * A_STAGE_COLS);
+                        uint64_t db = db0[0];
 #pragma unroll
-                    for (int s = 1; s < ESTAGES; s++)
-                        if (se == s) db = db0[s];
+                        for (int s = 1; s < ESTAGES; s++)
+                            if (se == s) db = db0[s];
 #pragma unroll
-                    for (int j = 0; j < KS / MMA_K; j++)
-                        mma_f8_ta(tmem + ACC_COL, ta + j * (MMA_K / 4), db + 2 * j, idesc,
-                                  (kin > 0 || sub > 0 || j > 0) ? 1u : 0u);
-                    mma_commit(empty_e(se));
-                }
-                kin += SUB;
-                ks += SUB;
-                if (kin >= kchunk || ks == nks) {
-                    mma_commit(acc_full);
-                    seg++;
-                    kin = 0;
-                    if (ks == nks) ks = 0;
+                        for (int j = 0; j < KS / MMA_K; j++)
+                            mma_f8_ta(tmem + ACC_COL, ta + j * (MMA_K / 4), db + 2 * j, idesc,
+                                      (kin > 0 || sub > 0 || j > 0) ? 1u : 0u);
+                        mma_commit(empty_e(se));
+                    }
+                    kin += SUB;
+                    if (kin >= kchunk || ks + SUB >= nks) {
+                        mma_commit(acc_full);
+                        seg++;
+                        kin = 0;
+                    }
                 }
             }
             if (!ok) {  // wait (bounded) for every MMA this thread issued
@@ -533,11 +599,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         // ---------------------------------------------------- epilogue
         const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
         const uint32_t tlane = (uint32_t)(32 * quarter) << 16;
-        const int nseg = (nks + kchunk - 1) / kchunk;
         int seg = 0;
         bool ok = true;
-        for (int t = blockIdx.x; ok && t < p.total_tiles; t += gridDim.x) {
-            const TileCoord tc = tile_of(t, p.tiles_m, p.tiles_n);
+        for (int i = 0; ok && i < my_tiles; i++) {
+            const Tile tc = tile_get<BATCHED>(p, i, &tmA, &tmB);
+            const int nseg = (tc.nks + kchunk - 1) / kchunk;
+            const bool gf2 = tc.op == OP_GF2;
             uint32_t words[BN / 32];
 #pragma unroll
             for (int c = 0; c < BN / 32; c++) words[c] = 0u;
@@ -551,11 +618,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int c = 0; c < BN / 32; c++) {
                     uint32_t v[32];
                     tmem_ld32(tmem + tlane + (uint32_t)(ACC_COL + 32 * c), v);
-                    const uint32_t wbits = pack_bits<OP>(v);
-                    if (OP == OP_GF2)
-                        words[c] ^= wbits;
+                    if (gf2)
+                        words[c] ^= pack_bits<OP_GF2>(v);
                     else
-                        words[c] |= wbits;
+                        words[c] |= pack_bits<OP_BOOL>(v);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -563,10 +629,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             if (!ok) break;
             const int64_t row = (int64_t)tc.tm * BM + 32 * quarter + lane;
-            if (row < p.m) {
-                uint64_t* crow = p.C + (int64_t)tc.leaf * p.strideC + row * p.ldc;
+            if (row < tc.m) {
+                uint64_t* crow = tc.C + row * tc.ldc;
                 const int64_t w0 = (int64_t)tc.tn * (BN / 64);
-                const int64_t nw = p.n / 64;
+                const int64_t nw = tc.n / 64;
 #pragma unroll
                 for (int c = 0; c < BN / 64; c++)
                     if (w0 + c < nw)
@@ -618,20 +684,25 @@ bool make_map(CUtensorMap* map, const uint64_t* base, int64_t kwords, int64_t ro
     return r == CUDA_SUCCESS;
 }
 
-template <int OP>
-cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const Params& prm,
+template <bool BATCHED>
+cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const Params& prm, int grid,
                       cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_nt_kernel<OP>,
+        cudaError_t e = cudaFuncSetAttribute(tc_nt_kernel<BATCHED>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int grid = prm.total_tiles < sm_count() ? prm.total_tiles : sm_count();
-    tc_nt_kernel<OP><<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, prm);
+    tc_nt_kernel<BATCHED><<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, prm);
     return cudaGetLastError();
+}
+
+Spread spread_factors() {
+    Spread sp;
+    for (int j = 0; j < 8; j++) sp.f[j] = j <= 3 ? (1u << (3 - j)) : (1u << (35 - j));
+    return sp;
 }
 
 }  // namespace
@@ -662,13 +733,14 @@ bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int6
     if (!make_map(&ma, A, k / 64, m, lda, count, strideA, BM) ||
         !make_map(&mb, Bt, k / 64, n, ldb, count, strideB, BN))
         return BMM_ERR_CUDA;
-    Params prm;
+    Params prm{};
     prm.C = C;
     prm.ldc = ldc;
     prm.strideC = strideC;
     prm.m = (int)m;
     prm.n = (int)n;
     prm.nks = (int)((k + KP - 1) / KP) * SUB;  // whole packed stages; the tail is zero-filled
+    prm.op = op;
     prm.kchunk = tc_kchunk_stages(path, prm.nks);
     prm.tiles_m = (int)((m + BM - 1) / BM);
     prm.tiles_n = (int)((n + BN - 1) / BN);
@@ -676,12 +748,49 @@ bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int6
     if (total > 0x7fffffff) return BMM_ERR_UNSUPPORTED;
     prm.total_tiles = (int)total;
     prm.err = err;
-    for (int j = 0; j < 8; j++) prm.sp.f[j] = j <= 3 ? (1u << (3 - j)) : (1u << (35 - j));
+    prm.sp = spread_factors();
     TraceScope ts(BMM_PHASE_BASE, s);
-    const cudaError_t e =
-        (op == OP_GF2) ? launch_tc<OP_GF2>(ma, mb, prm, s) : launch_tc<OP_BOOL>(ma, mb, prm, s);
+    const int grid = prm.total_tiles < sm_count() ? prm.total_tiles : sm_count();
+    const cudaError_t e = launch_tc<false>(ma, mb, prm, grid, s);
     if (e != cudaSuccess) return cuda_fail(e);
     return BMM_OK;
+}
+
+}  // namespace bmm
+
+namespace bmm {
+
+bool tc_make_problem(TcProblem* out, const uint64_t* A, int64_t lda, const uint64_t* Bt,
+                     int64_t ldb, uint64_t* C, int64_t ldc, int64_t m, int64_t k, int64_t n,
+                     int op) {
+    if (k % KS || (lda & 1) || (ldb & 1)) return false;
+    if (!make_map(&out->mapA, A, k / 64, m, lda, 1, 0, BM) ||
+        !make_map(&out->mapB, Bt, k / 64, n, ldb, 1, 0, BN))
+        return false;
+    out->C = C;
+    out->ldc = ldc;
+    out->m = (int32_t)m;
+    out->n = (int32_t)n;
+    out->nks = (int32_t)(((k + KP - 1) / KP) * SUB);
+    out->op = op;
+    return true;
+}
+
+cudaError_t tc_launch_batched(const TcProblem* d_probs, const TcWorkItem* d_items,
+                              const int32_t* d_cta_ptr, int grid, cudaStream_t s) {
+    uint32_t* err = device_error_word();
+    if (!err) return cudaErrorMemoryAllocation;
+    Params prm{};
+    prm.probs = d_probs;
+    prm.items = d_items;
+    prm.cta_ptr = d_cta_ptr;
+    prm.kchunk = 65534;
+    prm.err = err;
+    prm.sp = spread_factors();
+    CUtensorMap dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    TraceScope ts(BMM_PHASE_BASE, s);
+    return launch_tc<true>(dummy, dummy, prm, grid, s);
 }
 
 }  // namespace bmm

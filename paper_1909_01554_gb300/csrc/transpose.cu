@@ -25,15 +25,16 @@ __device__ __forceinline__ uint64_t swap_step(uint64_t v, int lane, int j, uint6
     return v ^ t;
 }
 
-__global__ void __launch_bounds__(256) transpose_kernel(const uint64_t* __restrict__ X,
-                                                        int64_t pitch, uint64_t* __restrict__ Xt,
-                                                        int64_t tpitch, int64_t rows,
-                                                        int64_t cols) {
+// One CTA tile: input rows [256 by, 256 by + 256), words [4 bx, 4 bx + 4).
+__device__ __forceinline__ void transpose_tile(const uint64_t* __restrict__ X, int64_t pitch,
+                                               uint64_t* __restrict__ Xt, int64_t tpitch,
+                                               int64_t rows, int64_t cols, int64_t bx,
+                                               int64_t by) {
     __shared__ uint64_t tin[TILE_R][PADW];
     __shared__ uint64_t tout[TILE_W * 64][PADW];
     const int t = threadIdx.x;
-    const int64_t r0 = (int64_t)blockIdx.y * TILE_R;
-    const int64_t w0 = (int64_t)blockIdx.x * TILE_W;  // first input word (column / 64)
+    const int64_t r0 = by * TILE_R;
+    const int64_t w0 = bx * TILE_W;  // first input word (column / 64)
     const int64_t xw = cols / 64, tw = rows / 64;
 
     {
@@ -78,6 +79,31 @@ __global__ void __launch_bounds__(256) transpose_kernel(const uint64_t* __restri
     }
 }
 
+
+__global__ void __launch_bounds__(256) transpose_kernel(const uint64_t* __restrict__ X,
+                                                        int64_t pitch, uint64_t* __restrict__ Xt,
+                                                        int64_t tpitch, int64_t rows,
+                                                        int64_t cols) {
+    transpose_tile(X, pitch, Xt, tpitch, rows, cols, blockIdx.x, blockIdx.y);
+}
+
+// Many transposes in one launch: CTA b takes tile b - first[i] of problem i,
+// where first[] is the exclusive prefix of the problems' tile counts.
+__global__ void __launch_bounds__(256) transpose_batched_kernel(const TransposeJob* __restrict__ jobs,
+                                                                const int64_t* __restrict__ first,
+                                                                int count) {
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {  // last i with first[i] <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const TransposeJob j = jobs[lo];
+    const int64_t local = b - first[lo];
+    const int64_t gx = (j.cols / 64 + TILE_W - 1) / TILE_W;
+    transpose_tile(j.X, j.pitch, j.Xt, j.tpitch, j.rows, j.cols, local % gx, local / gx);
+}
+
 }  // namespace
 
 cudaError_t launch_transpose_pitched(const uint64_t* X, int64_t pitch, uint64_t* Xt,
@@ -90,6 +116,19 @@ cudaError_t launch_transpose_pitched(const uint64_t* X, int64_t pitch, uint64_t*
     TraceScope ts(BMM_PHASE_TRANSPOSE, s);
     transpose_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(X, pitch, Xt, tpitch, rows,
                                                                       cols);
+    return cudaGetLastError();
+}
+
+int64_t transpose_tiles(int64_t rows, int64_t cols) {
+    return ((cols / 64 + TILE_W - 1) / TILE_W) * ((rows + TILE_R - 1) / TILE_R);
+}
+
+cudaError_t launch_transpose_batched(const TransposeJob* jobs, const int64_t* first, int count,
+                                     int64_t total_tiles, cudaStream_t s) {
+    if (count <= 0 || total_tiles <= 0) return cudaSuccess;
+    if (total_tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    TraceScope ts(BMM_PHASE_TRANSPOSE, s);
+    transpose_batched_kernel<<<(unsigned)total_tiles, 256, 0, s>>>(jobs, first, count);
     return cudaGetLastError();
 }
 

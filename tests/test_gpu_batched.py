@@ -1,0 +1,141 @@
+"""Batched uneven products (one persistent launch) against the CPU oracle.
+
+Problem i of a batch draws its inputs from the generator with seed
+base * 2^16 + i (A: matrix id 0, B: matrix id 1)."""
+import numpy as np
+import pytest
+
+import bitgen
+import oracle as O
+from gpu_util import first_mismatch, from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU machine
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_1909_01554_gb300 as bmm  # noqa: E402
+
+
+def density(op, k):
+    return None if op == bmm.GF2 else f"1/sqrt({k})"
+
+
+def make_batch(shapes, base_seed):
+    host, dev = [], []
+    for i, (m, k, n, op) in enumerate(shapes):
+        seed = (base_seed << 16) + i
+        A = bitgen.fill_cpu(m, k, seed, 0, p=density(op, k))
+        B = bitgen.fill_cpu(k, n, seed, 1, p=density(op, k))
+        host.append((A, B))
+        C = bmm.empty(m, n)
+        C.fill_(-1)
+        dev.append((to_dev(A), to_dev(B), C))
+    return host, dev
+
+
+def check_all(shapes, host, dev, which=None):
+    for i, ((m, k, n, op), (A, B), (_, _, C)) in enumerate(zip(shapes, host, dev)):
+        if which is not None and i not in which:
+            continue
+        want = O.cubic(O.GF2 if op == bmm.GF2 else O.BOOL, A, B, m, k, n)
+        mm = first_mismatch(from_dev(C, m, n), want)
+        assert mm is None, f"problem {i} {(m, k, n, op)}: {mm}"
+
+
+SMALL = [(64, 64, 64, 0), (192, 320, 448, 1), (384, 1152, 320, 0), (128, 256, 256, 1),
+         (576, 704, 832, 0), (256, 128, 64, 1), (1024, 960, 1088, 0), (64, 2048, 192, 1)]
+
+
+def test_batched_mixed_small():
+    host, dev = make_batch(SMALL, 41)
+    ops = [s[3] for s in SMALL]
+    bmm.batched(ops, [d[0] for d in dev], [d[1] for d in dev], [d[2] for d in dev],
+                [s[0] for s in SMALL], [s[1] for s in SMALL], [s[2] for s in SMALL])
+    bmm.stream_status()
+    check_all(SMALL, host, dev)
+
+
+def test_uniform_op_batched_entry_points():
+    shapes = [(s[0], s[1], s[2], 0) for s in SMALL[:4]]
+    host, dev = make_batch(shapes, 42)
+    L = bmm.lib()
+    import ctypes
+
+    arr = bmm._batch_arrays([0] * 4, [d[0] for d in dev], [d[1] for d in dev],
+                            [d[2] for d in dev], [s[0] for s in shapes], [s[1] for s in shapes],
+                            [s[2] for s in shapes])
+    st = L.bmm_gf2_batched(arr[0], *arr[2:], ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == bmm.OK
+    check_all(shapes, host, dev)
+
+
+def test_plan_reuse_and_graph_replay():
+    shapes = bitgen.batched_shapes(48, 7, lo=256, hi=1536)
+    host, dev = make_batch(shapes, 43)
+    plan = bmm.BatchedPlan([s[3] for s in shapes], [d[0] for d in dev], [d[1] for d in dev],
+                           [d[2] for d in dev], [s[0] for s in shapes], [s[1] for s in shapes],
+                           [s[2] for s in shapes])
+    plan.run()
+    bmm.stream_status()
+    check_all(shapes, host, dev)
+    # new data in the same buffers, replayed through a captured CUDA graph
+    host2 = []
+    for i, ((m, k, n, op), (dA, dB, dC)) in enumerate(zip(shapes, dev)):
+        seed = (44 << 16) + i
+        A = bitgen.fill_cpu(m, k, seed, 0, p=density(op, k))
+        B = bitgen.fill_cpu(k, n, seed, 1, p=density(op, k))
+        dA.copy_(to_dev(A))
+        dB.copy_(to_dev(B))
+        dC.fill_(-1)
+        host2.append((A, B))
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    bmm.stream_status()
+    check_all(shapes, host2, dev)
+    plan.destroy()
+
+
+def test_batched_config5_shapes_sampled():
+    """2048 problems, m, k, n log-uniform in [256, 8192] (multiples of 64), 50/50
+    GF(2)/Boolean, seed 5: every problem checked on two oracle rows, 12 in full."""
+    shapes = bitgen.batched_shapes(2048, 5)
+    dev, rows = [], []
+    rng = np.random.default_rng(5)
+    for i, (m, k, n, op) in enumerate(shapes):
+        seed = (5 << 16) + i
+        A = bmm.empty(m, k)
+        B = bmm.empty(k, n)
+        bitgen.fill_device(A, k, seed, 0, p=density(op, k))
+        bitgen.fill_device(B, k, seed, 1, p=density(op, k))
+        C = bmm.empty(m, n)
+        C.fill_(-1)
+        dev.append((A, B, C))
+        rows.append(sorted(rng.choice(m, 2, replace=False).tolist()))
+    torch.cuda.synchronize()
+    bmm.batched([s[3] for s in shapes], [d[0] for d in dev], [d[1] for d in dev],
+                [d[2] for d in dev], [s[0] for s in shapes], [s[1] for s in shapes],
+                [s[2] for s in shapes])
+    bmm.stream_status()
+    full = set(rng.choice(2048, 12, replace=False).tolist())
+    for i, (m, k, n, op) in enumerate(shapes):
+        seed = (5 << 16) + i
+        p = density(op, k)
+        B = bitgen.fill_cpu(k, n, seed, 1, p=p)
+        got = from_dev(dev[i][2], m, n)
+        o = O.GF2 if op == bmm.GF2 else O.BOOL
+        if i in full:
+            A = bitgen.fill_cpu(m, k, seed, 0, p=p)
+            mm = first_mismatch(got, O.cubic(o, A, B, m, k, n))
+            assert mm is None, f"problem {i} {(m, k, n, op)}: {mm}"
+        else:
+            for r in rows[i]:
+                Ar = bitgen.fill_cpu(m, k, seed, 0, p=p, row0=r, nrows=1)
+                want = O.rows(o, Ar, B, k, n)
+                assert (got[r] == want[0]).all(), f"problem {i} row {r}"

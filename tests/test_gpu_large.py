@@ -1,0 +1,117 @@
+"""Full-size products (the benchmark's configurations) checked on outputs the
+oracle computes one by one: sampled rows (oracle rows against the whole B),
+sampled columns (oracle column against the whole A), and for GF(2) Freivalds
+checks C x == A (B x) with seeded random vectors (a wrong C passes one vector
+with probability <= 1/2).
+
+Inputs on the GPU come from the device generator; the oracle's inputs come
+from the CPU generator (the two are checked equal in test_gpu_parity)."""
+import os
+
+import numpy as np
+import pytest
+
+import bitgen
+import oracle as O
+from gpu_util import from_dev
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU machine
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_1909_01554_gb300 as bmm  # noqa: E402
+
+IDS_GF2 = (0, 1)
+IDS_BOOL = (4, 5)
+
+
+def dev_gen(rows, cols, seed, mid, p):
+    t = bmm.empty(rows, cols)
+    bitgen.fill_device(t, cols, seed, mid, p=p, stream=torch.cuda.current_stream().cuda_stream)
+    return t
+
+
+def sampled_check(op, n, seed, ids, p, C, nrows=8, ncols=8, freivalds=8):
+    """C (host, n x n/64 words) against oracle rows, columns and Freivalds."""
+    rng = np.random.default_rng(seed * 7919 + op)
+    o = O.GF2 if op == bmm.GF2 else O.BOOL
+    B = bitgen.fill_cpu(n, n, seed, ids[1], p=p)
+    rows = sorted(rng.choice(n, nrows, replace=False).tolist())
+    Ar = np.concatenate([bitgen.fill_cpu(n, n, seed, ids[0], p=p, row0=r, nrows=1) for r in rows])
+    want_rows = O.rows(o, Ar, B, n, n)
+    for i, r in enumerate(rows):
+        assert (C[r] == want_rows[i]).all(), f"row {r}"
+    A = bitgen.fill_cpu(n, n, seed, ids[0], p=p)
+    for j in sorted(rng.choice(n, ncols, replace=False).tolist()):
+        want = O.column(o, A, B, j, n, n, n)
+        got = ((C[:, j // 64] >> np.uint64(j % 64)) & np.uint64(1)).astype(np.uint8)
+        assert (got == want).all(), f"column {j}"
+    if op == bmm.GF2:
+        for _ in range(freivalds):
+            x = rng.integers(0, np.iinfo(np.uint64).max, size=n // 64, dtype=np.uint64,
+                             endpoint=True)
+            assert (O.matvec_gf2(C, x, n, n) ==
+                    O.matvec_gf2(A, O.matvec_gf2(B, x, n, n), n, n)).all(), "Freivalds"
+    # Boolean output density: k p^2 = 1 in every Boolean workload -> 1 - 1/e
+    if op == bmm.BOOL:
+        dens = np.unpackbits(C[:: max(1, n // 512)].view(np.uint8)).mean()
+        assert abs(dens - (1 - np.exp(-1))) < 0.02
+
+
+def run_product(op, n, seed, ids, p, **kw):
+    A = dev_gen(n, n, seed, ids[0], p)
+    B = dev_gen(n, n, seed, ids[1], p)
+    C = bmm.empty(n, n)
+    C.fill_(-1)
+    bmm.product(op, A, B, C, n, n, n, **kw)
+    bmm.stream_status()
+    out = from_dev(C, n, n)
+    del A, B, C
+    torch.cuda.empty_cache()
+    return out
+
+
+def test_config2_square32768_bench_launch_configuration():
+    """m = k = n = 32768, seed 2: GF(2) p = 1/2 through the planner's default
+    (2-level self-inverse Strassen on the tensor base case), Boolean p = 2^-7.5
+    cubic - exactly the calls bench.py times."""
+    n, seed = 32768, 2
+    info = bmm.plan(bmm.GF2, n, n, n)
+    assert info["strassen_depth"] == 2 and info["leaves"] == 49
+    Cg = run_product(bmm.GF2, n, seed, IDS_GF2, None)
+    sampled_check(bmm.GF2, n, seed, IDS_GF2, None, Cg)
+    Cb = run_product(bmm.BOOL, n, seed, IDS_BOOL, "2^-7.5")
+    sampled_check(bmm.BOOL, n, seed, IDS_BOOL, "2^-7.5", Cb)
+
+
+def test_config3_square65536_paths_agree():
+    """m = k = n = 65536, seed 3: the tensor-core and CUDA-core base cases give
+    bit-identical products (cubic), and both match the oracle's samples; the
+    planner's Strassen product matches too. GF(2) p = 1/2, Boolean p = 2^-8."""
+    n, seed = 65536, 3
+    if not bmm.device_supported():
+        pytest.skip("tensor-core path needs sm_103")
+    for op, ids, p in ((bmm.GF2, IDS_GF2, None), (bmm.BOOL, IDS_BOOL, "2^-8")):
+        tc = run_product(op, n, seed, ids, p, path=bmm.PATH_TC_FP8, depth=0)
+        pc = run_product(op, n, seed, ids, p, path=bmm.PATH_POPC, depth=0)
+        assert (tc == pc).all(), f"tensor vs CUDA-core disagree (op={op})"
+        if op == bmm.GF2:
+            st = run_product(op, n, seed, ids, p)
+            assert (st == tc).all(), "Strassen vs cubic disagree"
+        sampled_check(op, n, seed, ids, p, tc, nrows=4, ncols=4, freivalds=4)
+
+
+@pytest.mark.skipif(os.environ.get("BMM_TEST_2POW19") != "1",
+                    reason="m = k = n = 2^19 (32 GiB per operand, minutes): set BMM_TEST_2POW19=1")
+def test_config4_square524288():
+    """m = k = n = 2^19, seed 4: GF(2) p = 1/2 through the planner's Strassen
+    (depth-first top levels so that it fits HBM), Boolean p = 2^-9.5 cubic;
+    sampled rows and columns plus GF(2) Freivalds."""
+    n, seed = 1 << 19, 4
+    Cg = run_product(bmm.GF2, n, seed, IDS_GF2, None)
+    sampled_check(bmm.GF2, n, seed, IDS_GF2, None, Cg, nrows=4, ncols=4, freivalds=4)
+    del Cg
+    Cb = run_product(bmm.BOOL, n, seed, IDS_BOOL, "2^-9.5")
+    sampled_check(bmm.BOOL, n, seed, IDS_BOOL, "2^-9.5", Cb, nrows=4, ncols=4, freivalds=0)

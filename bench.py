@@ -35,6 +35,10 @@ WORKLOADS = {
     "square32768": (32768, 2, "2^-7.5"),
     "square4096": (4096, 1, "1/64"),
     "square65536": (65536, 3, "2^-8"),
+    "square524288": (524288, 4, "2^-9.5"),
+    # 2048 problems, m, k, n log-uniform in [256, 8192] (multiples of 64), 50/50
+    # GF(2) (p = 1/2) / Boolean (p = 1/sqrt(k)); problem i uses seed 5 * 2^16 + i
+    "batched2048": (2048, 5, "1/sqrt(k)"),
 }
 DEFAULT_WORKLOAD = "square32768"
 # Matrix ids of the generator streams: GF(2) pair (0, 1), Boolean pair (4, 5).
@@ -160,6 +164,29 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.workload.startswith("batched"):
+        count, seed, _ = WORKLOADS[args.workload]
+        probs = batched_problems(count, seed)
+        for _ in range(args.warmup):
+            oracle_batched_sample(probs, 1.0)
+        tot_s, tot_b, used, th = 0.0, 0, 0, 1
+        for _ in range(args.steps):
+            dt, b, used, th = oracle_batched_sample(probs, 3.0)
+            tot_s += dt
+            tot_b += b
+        value = tot_b / tot_s
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "bop/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (seeded SplitMix64 Bernoulli bits)",
+            "config": {"workload": args.workload, "problems": count},
+            "cpu_baseline": {"value": value, "unit": "bop/s", "cores": th, "kind": "oracle",
+                             "sample": f"the first {used} problems of the batch per step"},
+            "e2e": {"value": value, "unit": "bop/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}), flush=True)
+        return 0
     n, seed, bool_p = WORKLOADS[args.workload]
     rows = calibrated_rows(n, seed, bool_p, 3.0)
     for _ in range(args.warmup):
@@ -191,6 +218,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload.startswith("batched"):
+        return run_batched(args)
 
     import torch
 
@@ -352,6 +381,202 @@ def main():
             "phases_ms_per_step": {"base": base_ms / args.steps, "xor": xor_ms / args.steps,
                                    "transpose": tr_ms / args.steps},
             "phase_launches": {"base": base_n, "xor": xor_n, "transpose": tr_n},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+
+def batched_problems(count: int, seed: int):
+    import bitgen
+
+    shapes = bitgen.batched_shapes(count, seed)
+    return [(m, k, n, op, (seed << 16) + i) for i, (m, k, n, op) in enumerate(shapes)]
+
+
+def density_for(op: int, k: int):
+    return None if op == 0 else f"1/sqrt({k})"
+
+
+def oracle_batched_sample(probs, target_s: float):
+    """Oracle time on whole problems of the batch, taken in order until about
+    target_s seconds. Returns (seconds, bit operations, problems, threads)."""
+    import bitgen
+    import oracle
+
+    tot_s, bops, used = 0.0, 0, 0
+    th = oracle.threads()
+    for m, k, n, op, seed in probs:
+        A = bitgen.fill_cpu(m, k, seed, 0, p=density_for(op, k))
+        B = bitgen.fill_cpu(k, n, seed, 1, p=density_for(op, k))
+        t0 = time.perf_counter()
+        oracle.cubic(oracle.GF2 if op == 0 else oracle.BOOL, A, B, m, k, n, th)
+        tot_s += time.perf_counter() - t0
+        bops += 2 * m * k * n
+        used += 1
+        if tot_s >= target_s:
+            break
+    return tot_s, bops, used, th
+
+
+def run_batched(args):
+    import torch
+
+    import bitgen
+    import paper_1909_01554_gb300 as bmm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    count, seed, _ = WORKLOADS[args.workload]
+    probs = batched_problems(count, seed)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    As, Bs, Cs = [], [], []
+    with torch.cuda.stream(stream):
+        for m, k, n, op, sd in probs:
+            A, B = bmm.empty(m, k), bmm.empty(k, n)
+            bitgen.fill_device(A, k, sd, 0, p=density_for(op, k), stream=sh)
+            bitgen.fill_device(B, n, sd, 1, p=density_for(op, k), stream=sh)
+            As.append(A)
+            Bs.append(B)
+            Cs.append(bmm.empty(m, n))
+    torch.cuda.synchronize()
+    ops = [p[3] for p in probs]
+    ms, ks, ns = [p[0] for p in probs], [p[1] for p in probs], [p[2] for p in probs]
+    bops_step = sum(2 * m * k * n for m, k, n, *_ in probs)
+
+    plan = bmm.BatchedPlan(ops, As, Bs, Cs, ms, ks, ns)
+    graph = torch.cuda.CUDAGraph()
+    plan.run(stream=sh)  # warm the kernels before capture
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, stream=stream):
+        plan.run(stream=sh)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            graph.replay()
+    torch.cuda.synchronize()
+    bmm.stream_status(sh)
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    bmm.trace_enable(True)
+    l0 = bmm.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    bmm.trace_enable(False)
+    # a graph replay launches the kernels a plan run launches: the batched
+    # transpose, the row padding (when some k/64 is odd) and the base case
+    per_run = 3 if any((k // 64) % 2 for k in ks) else 2
+    launches = (bmm.launch_count() - l0) + per_run * args.steps
+    ms_total = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = world * bops_step * args.steps / (ms_total / 1000.0)
+
+    # the base-case kernel alone, timed with events on its stream (one plan run)
+    bmm.trace_enable(True)
+    plan.run(stream=sh)
+    torch.cuda.synchronize()
+    bmm.trace_enable(False)
+    base_n, base_ms = bmm.trace_read(bmm.PHASE_BASE)
+    pk, pk_kind = peaks()
+    peak = pk["bf16_tflops_sustained"] * FP8_PER_BF16
+    achieved = bops_step / (base_ms / 1000.0) / 1e12 if base_ms > 0 else 0.0
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": f"{pk_kind} bf16 sustained x {FP8_PER_BF16} (nominal fp8:bf16)"}
+
+    # the same products as one library call per problem
+    def per_problem():
+        for (m, k, n, op, _), A, B, C in zip(probs, As, Bs, Cs):
+            bmm.product(op, A, B, C, m, k, n, stream=sh)
+
+    per_problem()
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    p0.record(stream)
+    per_problem()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    per_ms = p0.elapsed_time(p1)
+    per_wall = (time.perf_counter() - t0) * 1000
+
+    # end to end: inputs from pinned host memory, products back to the host
+    e2e = None
+    if not args.no_e2e:
+        hA = [a.cpu().pin_memory() for a in As]
+        hB = [b.cpu().pin_memory() for b in Bs]
+        hC = [torch.empty_like(c, device="cpu").pin_memory() for c in Cs]
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                for h, d in zip(hA, As):
+                    d.copy_(h, non_blocking=True)
+                for h, d in zip(hB, Bs):
+                    d.copy_(h, non_blocking=True)
+                graph.replay()
+                for h, d in zip(hC, Cs):
+                    h.copy_(d, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        e2e = {"value": world * bops_step * args.steps / (ems / 1000.0), "unit": "bop/s",
+               "h2d_bytes_per_step": sum(a.numel() * 8 for a in As + Bs),
+               "d2h_bytes_per_step": sum(c.numel() * 8 for c in Cs)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        tot_s, b, used, th = oracle_batched_sample(probs, 12.0)
+        cpu = {"value": b / tot_s, "unit": "bop/s", "cores": th, "kind": "oracle",
+               "sample": f"the first {used} of {count} problems, whole ({tot_s:.1f} s)"}
+    plan.destroy()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "bop/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e4m3",
+            "data": "synthetic (seeded SplitMix64 Bernoulli bits)",
+            "config": {"workload": args.workload, "problems": count,
+                       "shapes": "m, k, n log-uniform in [256, 8192], multiples of 64",
+                       "ops": "50/50 GF(2) (p=1/2) / Boolean (p=1/sqrt(k))",
+                       "sum_2mkn": bops_step, "launch": "one CUDA-graph replay of a batch plan "
+                       "(batched transpose, row padding, persistent tcgen05 base case)",
+                       "l2": "inputs larger than L2 (~4 GB per step)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks,
+            "per_problem_launches": {"value": bops_step / (per_ms / 1000.0), "unit": "bop/s",
+                                     "ms": per_ms, "host_wall_ms": per_wall,
+                                     "launches": None},
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -222,6 +222,13 @@ int64_t bmm_launch_count(void);
  * last call (BMM_ERR_TIMEOUT after a bounded wait gave up), else BMM_OK. */
 bmm_status bmm_stream_status(bmm_stream_t stream);
 
+/* Launches one thread that waits, with the same bounded wait the kernels
+ * use, on a barrier nothing ever arrives on, for limit_ns nanoseconds (at
+ * most 10 s). The wait gives up, records the timeout and the kernel returns;
+ * the next bmm_stream_status() reports BMM_ERR_TIMEOUT and clears it. A test
+ * of the failure path that faults and hangs nothing. */
+bmm_status bmm_selftest_wait_timeout(int64_t limit_ns, bmm_stream_t stream);
+
 /* Name of a status code (static string). */
 const char *bmm_status_string(bmm_status status);
 

@@ -26,7 +26,7 @@ EXPORTED = [
     "bmm_gf2_batched", "bmm_bool_batched", "bmm_batched", "bmm_batched_plan_create",
     "bmm_batched_plan_run", "bmm_batched_plan_destroy", "bmm_transpose", "bmm_base_product",
     "bmm_basis_change", "bmm_stream_status", "bmm_status_string", "bmm_last_cuda_error",
-    "bmm_device_supported", "bmm_plan", "bmm_product_noalloc", "bmm_trace_enable", "bmm_trace_read", "bmm_launch_count",
+    "bmm_device_supported", "bmm_plan", "bmm_product_noalloc", "bmm_selftest_wait_timeout", "bmm_trace_enable", "bmm_trace_read", "bmm_launch_count",
 ]
 PHASE_BASE, PHASE_XOR, PHASE_TRANSPOSE = 0, 1, 2
 
@@ -103,6 +103,8 @@ def _lib_handle():
         L.bmm_plan.restype = i32
         L.bmm_product_noalloc.argtypes = [i32, vp, vp, vp, i64, i64, i64, vp]
         L.bmm_product_noalloc.restype = i32
+        L.bmm_selftest_wait_timeout.argtypes = [i64, vp]
+        L.bmm_selftest_wait_timeout.restype = i32
         L.bmm_trace_enable.argtypes = [i32]
         L.bmm_trace_enable.restype = None
         L.bmm_trace_read.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]

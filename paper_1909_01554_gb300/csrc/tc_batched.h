@@ -9,9 +9,9 @@
 
 namespace bmm {
 
-// One product of the batch, as the persistent kernel sees it (global memory,
-// 64-byte aligned so the TMA maps inside can be used in place).
-struct alignas(64) TcProblem {
+// One product of the batch, as the persistent kernel sees it (global memory;
+// CUtensorMap's own alignment keeps the TMA maps inside usable in place).
+struct TcProblem {
     CUtensorMap mapA;  // A (m x k), 3-D map (k words, m rows, 1)
     CUtensorMap mapB;  // Bt (n x k)
     uint64_t* C;

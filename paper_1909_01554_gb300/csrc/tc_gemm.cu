@@ -134,20 +134,16 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 
 // Bounded wait for the phase of `bar` with the given parity. Returns false
 // (after recording the timeout) if it did not complete within WAIT_NS.
-__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, uint32_t* err) {
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, uint32_t* err,
+                                            uint64_t limit_ns = WAIT_NS) {
     const uint64_t t0 = globaltimer();
     for (uint32_t i = 1;; i++) {
         if (mbar_try(bar, parity)) return true;
-        if ((i & 255u) == 0 && globaltimer() - t0 > WAIT_NS) {
+        if ((i & 255u) == 0 && globaltimer() - t0 > limit_ns) {
             atomicOr(err, DEVERR_TIMEOUT);
             return false;
         }
     }
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t* err) {
-    if (mbar_try(bar, parity)) return true;
-    return mbar_wait_slow(bar, parity, err);
 }
 
 __device__ __forceinline__ void fence_proxy_async() {
@@ -156,6 +152,21 @@ __device__ __forceinline__ void fence_proxy_async() {
 __device__ __forceinline__ void fence_barrier_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// Self-test of the bounded wait: one thread waits on a barrier that nothing
+// arrives on, gives up after limit_ns, records the timeout and returns.
+__global__ void wait_selftest_kernel(uint32_t* err, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    fence_barrier_init();
+    mbar_wait_slow(b, 0, err, limit_ns);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t* err) {
+    if (mbar_try(bar, parity)) return true;
+    return mbar_wait_slow(bar, parity, err);
+}
+
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -794,3 +805,13 @@ cudaError_t tc_launch_batched(const TcProblem* d_probs, const TcWorkItem* d_item
 }
 
 }  // namespace bmm
+
+extern "C" bmm_status bmm_selftest_wait_timeout(int64_t limit_ns, bmm_stream_t stream) {
+    using namespace bmm;
+    if (limit_ns <= 0 || limit_ns > 10000000000LL) return BMM_ERR_INVALID;
+    uint32_t* err = device_error_word();
+    if (!err) return BMM_ERR_NOMEM;
+    wait_selftest_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(err, (uint64_t)limit_ns);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BMM_OK : cuda_fail(e);
+}

@@ -194,6 +194,20 @@ def test_errors_are_reported():
     assert e.value.status == bmm.ERR_INVALID
 
 
+def test_bounded_wait_times_out_and_context_survives():
+    """A device-side wait that nothing satisfies gives up after its limit; the
+    host reads BMM_ERR_TIMEOUT and the context keeps working."""
+    stream = torch.cuda.current_stream().cuda_stream
+    assert bmm.lib().bmm_selftest_wait_timeout(20_000_000, stream) == bmm.OK  # 20 ms
+    with pytest.raises(bmm.BmmError) as e:
+        bmm.stream_status()
+    assert e.value.status == bmm.ERR_TIMEOUT
+    bmm.stream_status()  # cleared
+    n = 256
+    A, B = gen(n, n, 29, 0), gen(n, n, 29, 1)
+    check(run(bmm.GF2, A, B, n, n, n), O.cubic(O.GF2, A, B, n, n, n), "after timeout")
+
+
 def test_int8_tensor_path_is_unsupported_on_sm103():
     """sm_103a has no 8-bit integer tensor-core MMA: the path reports UNSUPPORTED."""
     d = bmm.empty(128, 128)

@@ -33,7 +33,6 @@ METRIC = "effective bop/s (2mkn/t) Boolean & GF(2) products, tensor-core vs popc
 # name: (n, seed, Boolean density); GF(2) operands are dense (p = 1/2).
 WORKLOADS = {
     "square32768": (32768, 2, "2^-7.5"),
-    "square4096": (4096, 1, "1/64"),
     "square65536": (65536, 3, "2^-8"),
     "square524288": (524288, 4, "2^-9.5"),
     # 2048 problems, m, k, n log-uniform in [256, 8192] (multiples of 64), 50/50
@@ -49,6 +48,22 @@ IDS_BOOL = (4, 5)
 LOP3_LANES_PER_SM_CLK = 64
 # Nominal dense FP8 : BF16 tensor throughput ratio (4.5 : 2.25 PFLOP/s).
 FP8_PER_BF16 = 2.0
+# FP8 MACs per clock per SM of tcgen05.mma kind::f8f6f4 on sm_103 (measured
+# with back-to-back MMAs); 2 FLOP each.
+FP8_MAC_PER_SM_CLK = 8192
+
+
+def tensor_pipe(achieved: float, clocks: dict, fallback_mhz: float) -> dict:
+    """The tensor pipe's own limit at the clock seen under load, beside the
+    measured-peak roofline."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or fallback_mhz
+    pp = sms * FP8_MAC_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
+    return {"pipe_peak": pp, "pipe_frac": achieved / pp,
+            "pipe_peak_source": f"{sms} SMs x {FP8_MAC_PER_SM_CLK} fp8 MAC/clk x 2 x "
+                                f"{mhz} MHz (median under load)"}
 
 
 def parse():
@@ -123,6 +138,24 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(x: float, dist) -> float:
+    """The largest x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_step: float, steps: int, ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time."""
+    return world * units_per_step * steps / (ms / 1000.0)
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -291,13 +324,10 @@ def main():
     base_n, base_ms = bmm.trace_read(bmm.PHASE_BASE)
     xor_n, xor_ms = bmm.trace_read(bmm.PHASE_XOR)
     tr_n, tr_ms = bmm.trace_read(bmm.PHASE_TRANSPOSE)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
 
     bops_step = 2 * (2 * m * k * n)
-    value = world * bops_step * args.steps / (ms / 1000.0)
+    value = job_rate(world, bops_step, args.steps, ms)
 
     # plan facts for the roofline of the base case (the dominant kernel)
     pg = bmm.plan(bmm.GF2, m, k, n, **kw_g)
@@ -312,7 +342,8 @@ def main():
         achieved = flops_base_step * args.steps / (base_ms / 1000.0) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{pk_kind} bf16 sustained x {FP8_PER_BF16} (nominal fp8:bf16)"}
+                "peak_source": f"{pk_kind} bf16 sustained x {FP8_PER_BF16} (nominal fp8:bf16)",
+                **tensor_pipe(achieved, clocks, pk["sm_max_mhz"])}
         dtype = "e4m3" if resolved == bmm.PATH_TC_FP8 else "u8"
     else:
         sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -349,11 +380,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ems = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ems], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * bops_step * args.steps / (ems / 1000.0), "unit": "bop/s",
+        ems = max_over_ranks(ems, dist)
+        e2e = {"value": job_rate(world, bops_step, args.steps, ems), "unit": "bop/s",
                "h2d_bytes_per_step": 4 * m * k // 8, "d2h_bytes_per_step": 2 * m * n // 8}
 
     cpu = None
@@ -371,7 +399,7 @@ def main():
                               f"self-inverse alternative basis",
                        "bool": f"p={bool_p}, cubic", "base_case": _path_name(resolved),
                        "bool_base_case": _path_name(pb["path"]),
-                       "l2": "inputs larger than L2 (each operand 128 MiB, ~1.7 GB per step)",
+                       "l2": f"inputs larger than L2 (each operand {m * k // 8 // 2**20} MiB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -488,11 +516,8 @@ def run_batched(args):
     per_run = 3 if any((k // 64) % 2 for k in ks) else 2
     launches = (bmm.launch_count() - l0) + per_run * args.steps
     ms_total = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    value = world * bops_step * args.steps / (ms_total / 1000.0)
+    ms_total = max_over_ranks(ms_total, dist)
+    value = job_rate(world, bops_step, args.steps, ms_total)
 
     # the base-case kernel alone, timed with events on its stream (one plan run)
     bmm.trace_enable(True)
@@ -505,7 +530,8 @@ def run_batched(args):
     achieved = bops_step / (base_ms / 1000.0) / 1e12 if base_ms > 0 else 0.0
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None,
-            "peak_source": f"{pk_kind} bf16 sustained x {FP8_PER_BF16} (nominal fp8:bf16)"}
+            "peak_source": f"{pk_kind} bf16 sustained x {FP8_PER_BF16} (nominal fp8:bf16)",
+            **tensor_pipe(achieved, clocks, pk["sm_max_mhz"])}
 
     # the same products as one library call per problem
     def per_problem():
@@ -548,8 +574,8 @@ def run_batched(args):
             e2e_step()
         e1.record(stream)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1)
-        e2e = {"value": world * bops_step * args.steps / (ems / 1000.0), "unit": "bop/s",
+        ems = max_over_ranks(e0.elapsed_time(e1), dist)
+        e2e = {"value": job_rate(world, bops_step, args.steps, ems), "unit": "bop/s",
                "h2d_bytes_per_step": sum(a.numel() * 8 for a in As + Bs),
                "d2h_bytes_per_step": sum(c.numel() * 8 for c in Cs)}
 

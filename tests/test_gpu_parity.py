@@ -105,6 +105,42 @@ def test_base_product_all_ones_large_k(path):
             assert (got == want).all(), f"k={k} op={op} path={path}"
 
 
+def prefix_rows(counts, k):
+    """Packed rows whose row r has exactly its first counts[r] bits set."""
+    kw = k // 64
+    c = torch.tensor(counts, dtype=torch.int64, device="cuda")[:, None]
+    idx = torch.arange(kw, dtype=torch.int64, device="cuda")[None, :]
+    rem = c % 64
+    part = torch.bitwise_left_shift(torch.ones_like(rem), rem) - 1  # rem = 0 gives 0
+    out = torch.where(idx < c // 64, torch.full_like(idx, -1),
+                      torch.where(idx == c // 64, part, torch.zeros_like(idx)))
+    return out.reshape(-1).contiguous()
+
+
+@pytest.mark.parametrize("path", paths())
+def test_base_product_exact_counts_past_2pow23(path):
+    """Prefix rows: entry (i, j) of the integer product is min(c_i, d_j), a closed
+    form. k = 2^23 + 2^21 bits takes the counts past 2^23, where the fp8 path
+    must flush its FP32 accumulator (it reads parity off count * 2^-12, exact
+    below 2^23), and puts every parity next to 2^22, 2^23 and k."""
+    m, n, k = 128, 256, (1 << 23) + (1 << 21)
+    rng = np.random.default_rng(31)
+    edge = [0, 1, 2, 63, 64, 65, (1 << 22) - 1, 1 << 22, (1 << 22) + 1,
+            65534 * 128 - 1, 65534 * 128, 65534 * 128 + 1, (1 << 23) - 1, 1 << 23,
+            (1 << 23) + 1, k - 1, k]
+    c = edge + rng.integers(0, k + 1, m - len(edge)).tolist()
+    d = [k] * (n // 2) + edge + rng.integers(0, k + 1, n // 2 - len(edge)).tolist()
+    A, Bt = prefix_rows(c, k), prefix_rows(d, k)
+    cnt = np.minimum(np.array(c)[:, None], np.array(d)[None, :])
+    for op in (bmm.GF2, bmm.BOOL):
+        dC = bmm.empty(m, n)
+        dC.fill_(-1)
+        bmm.base_product(op, path, A, Bt, dC, m, k, n)
+        bmm.stream_status()
+        want = O.pack(((cnt & 1) if op == bmm.GF2 else (cnt > 0)).astype(np.uint8))
+        check(from_dev(dC, m, n), want, f"large-count op={op} path={path}")
+
+
 # ------------------------------------------------------------ full products
 @pytest.mark.parametrize("op", [bmm.GF2, bmm.BOOL])
 @pytest.mark.parametrize("m,k,n", [(64, 128, 64), (448, 320, 576), (1024, 1024, 1024)])

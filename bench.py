@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
-    ap.add_argument("--path", choices=["auto", "fp8", "i8", "popc"], default="auto")
+    ap.add_argument("--path", choices=["auto", "fp8", "fp8pair", "i8", "popc"], default="auto")
     ap.add_argument("--depth", type=int, default=-1, help="Strassen depth of the GF(2) product")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -276,7 +276,7 @@ def main():
     n, seed, bool_p = WORKLOADS[args.workload]
     m = k = n
     path = {"auto": bmm.PATH_AUTO, "fp8": bmm.PATH_TC_FP8, "i8": bmm.PATH_TC_I8,
-            "popc": bmm.PATH_POPC}[args.path]
+            "popc": bmm.PATH_POPC, "fp8pair": bmm.PATH_TC_FP8_PAIR}[args.path]
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
 
@@ -337,14 +337,14 @@ def main():
     flops_base_step = 2 * leaves * lm * lk * ln + 2 * m * k * n  # GF(2) leaves + Boolean
     resolved = pg["path"]
     pk, pk_kind = peaks()
-    if resolved in (bmm.PATH_TC_FP8, bmm.PATH_TC_I8):
+    if resolved in (bmm.PATH_TC_FP8, bmm.PATH_TC_FP8_PAIR, bmm.PATH_TC_I8):
         peak = pk["bf16_tflops_sustained"] * FP8_PER_BF16
         achieved = flops_base_step * args.steps / (base_ms / 1000.0) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": f"{pk_kind} bf16 sustained x {FP8_PER_BF16} (nominal fp8:bf16)",
                 **tensor_pipe(achieved, clocks, pk["sm_max_mhz"])}
-        dtype = "e4m3" if resolved == bmm.PATH_TC_FP8 else "u8"
+        dtype = "u8" if resolved == bmm.PATH_TC_I8 else "e4m3"
     else:
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         peak = sms * LOP3_LANES_PER_SM_CLK * pk["sm_max_mhz"] * 1e6 * 64 / 1e12
@@ -612,7 +612,8 @@ def run_batched(args):
 
 def _path_name(p) -> str:
     return {1: "tcgen05 fp8 (e4m3, f32 accumulate)", 2: "tcgen05 int8 (u8, s32 accumulate)",
-            3: "CUDA-core LOP3/POPC"}.get(p, str(p))
+            3: "CUDA-core LOP3/POPC",
+            4: "tcgen05 fp8 (e4m3, f32 accumulate), SM pairs (cta_group::2)"}.get(p, str(p))
 
 
 if __name__ == "__main__":

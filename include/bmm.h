@@ -60,7 +60,8 @@ typedef enum {
     BMM_PATH_AUTO = 0,    /* the fastest path for the shape on this device */
     BMM_PATH_TC_FP8 = 1,  /* tcgen05 tensor cores, bits -> e4m3, FP32 accumulate */
     BMM_PATH_TC_I8 = 2,   /* tcgen05 tensor cores, bits -> u8, S32 accumulate */
-    BMM_PATH_POPC = 3     /* CUDA cores: LOP3 AND-XOR / AND-OR over 32-bit words */
+    BMM_PATH_POPC = 3,    /* CUDA cores: LOP3 AND-XOR / AND-OR over 32-bit words */
+    BMM_PATH_TC_FP8_PAIR = 4 /* as TC_FP8, two SMs per 256 x 256 tile (cta_group::2) */
 } bmm_path;
 
 /* 2x2 recursion for the binary product. */

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbmm.so")
 
 OK, ERR_INVALID, ERR_ALIGN, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
-PATH_AUTO, PATH_TC_FP8, PATH_TC_I8, PATH_POPC = 0, 1, 2, 3
+PATH_AUTO, PATH_TC_FP8, PATH_TC_I8, PATH_POPC, PATH_TC_FP8_PAIR = 0, 1, 2, 3, 4
 WINOGRAD, SELF_INVERSE, CHAINING = 0, 1, 2
 GF2, BOOL = 0, 1
 

@@ -21,6 +21,7 @@ cudaError_t launch_combine(int operand, const uint64_t* X, int64_t pitch, int64_
 cudaError_t launch_fold(const uint64_t* R, int64_t hr, int64_t hw, uint64_t* C, int64_t ldc,
                         uint32_t dest, uint32_t first, cudaStream_t s);
 bool tc_path_available();
+bool tc_pair_available();
 bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int64_t strideA,
                           const uint64_t* Bt, int64_t ldb, int64_t strideB, uint64_t* C,
                           int64_t ldc, int64_t strideC, int64_t count, int64_t m, int64_t k,
@@ -150,7 +151,7 @@ bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* op
     p.n = n;
     if (o.variant < 0 || o.variant > 2) return BMM_ERR_INVALID;
     p.variant = o.variant;
-    if (o.path < BMM_PATH_AUTO || o.path > BMM_PATH_POPC) return BMM_ERR_INVALID;
+    if (o.path < BMM_PATH_AUTO || o.path > BMM_PATH_TC_FP8_PAIR) return BMM_ERR_INVALID;
     if (o.path != BMM_PATH_AUTO && o.path != BMM_PATH_POPC && !tc_path_available())
         return BMM_ERR_UNSUPPORTED;
     // recursion depth
@@ -171,10 +172,15 @@ bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* op
         p.depth = d;
     }
     // base-case path: the tensor cores whenever the leaves allow TMA tiles
-    // (k of a leaf a multiple of 128 bits), else the CUDA-core kernel.
-    if (o.path == BMM_PATH_AUTO)
-        p.path = (tc_path_available() && ((k >> p.depth) % 128) == 0) ? BMM_PATH_TC_FP8
-                                                                        : BMM_PATH_POPC;
+    // (k of a leaf a multiple of 128 bits), as SM pairs where clusters can be
+    // launched (faster at every measured size from 4096^3 up), else the
+    // CUDA-core kernel.
+    if (o.path == BMM_PATH_AUTO) {
+        if (tc_path_available() && ((k >> p.depth) % 128) == 0)
+            p.path = tc_pair_available() ? BMM_PATH_TC_FP8_PAIR : BMM_PATH_TC_FP8;
+        else
+            p.path = BMM_PATH_POPC;
+    }
     else
         p.path = o.path;
     // depth-first levels: at least depth - MAX_MERGED; more while the

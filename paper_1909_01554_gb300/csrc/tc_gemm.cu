@@ -9,25 +9,34 @@
 // below 2^23). sm_103a has no 8-bit integer MMA (ptxas rejects
 // tcgen05.mma kind::i8 for this target), so FP8 is the exact tensor format.
 //
-// Persistent kernel, one CTA per SM, warp-specialised (22 warps):
-//   warp 20     TMA producer: packed tiles of 128 rows of A and 256 rows of
-//               Bt, 256 bits of k each (32-byte rows), into a PSTAGES-deep
-//               shared ring (cp.async.bulk.tensor, mbarrier complete_tx).
-//               Each packed stage feeds two operand stages of 128 bits.
-//   warps 8-15  A expansion: one row per thread, 256 bits -> 256 e4m3
-//               bytes (two operand stages) written straight into TMEM with
-//               tcgen05.st; two warps per TMEM lane quarter take alternate
-//               packed stages.
-//   warps 0-7   Bt expansion: each packed 32-bit word becomes 32 bytes of
+// Persistent kernel, one CTA per SM, warp-specialised (18 warps):
+//   warp 16     TMA producer: packed tiles of 128 rows of A and 256 rows of
+//               Bt (128 in a pair, below), 256 bits of k each (32-byte rows),
+//               into a PSTAGES-deep shared ring (cp.async.bulk.tensor,
+//               mbarrier complete_tx). Each packed stage feeds two operand
+//               stages of 128 bits.
+//   warps 4-11  A expansion: one row per thread, 256 bits -> 256 e4m3
+//               bytes (both operand stages) written straight into TMEM with
+//               one tcgen05.st; two warps per TMEM lane quarter take
+//               alternate packed stages.
+//   warps 0-3   Bt expansion: each packed 32-bit word becomes 32 bytes of
 //               the K-major, 128-byte-swizzled canonical UMMA layout; a warp
 //               expands 4 whole rows of a packed stage at a time.
-//   warp 21     MMA issuer: per packed stage, one wait, then for each of its
+//   warp 17     MMA issuer: per packed stage, one wait, then for each of its
 //               two operand stages 4 x tcgen05.mma (M=128, N=256, K=32; A
 //               from TMEM, B from shared memory) into the TMEM accumulator
 //               and one commit that frees that operand stage.
-//   warps 16-19 epilogue: tcgen05.ld 32 lanes x 32 columns at a time, parity
+//   warps 12-15 epilogue: tcgen05.ld 32 lanes x 32 columns at a time, parity
 //               or non-zero test, bits packed in registers with a shallow
 //               tree (one row per thread) and stored as 64-bit words.
+// SM pairs (PAIR): two CTAs of a cluster on two SMs share one 256 x 256 tile
+// through tcgen05.mma.cta_group::2 (M=256). Each CTA expands its own 128 rows
+// of A into its TMEM and its own 128 of the tile's 256 Bt rows into its
+// shared memory; the even CTA issues the MMAs, which read both CTAs'
+// operands and accumulate each CTA's 128 rows in its own TMEM. The gating
+// barriers (operand stage full, accumulator empty) live in the even CTA and
+// both CTAs' producers and epilogues arrive there; the commits that free an
+// operand stage or publish the accumulator are multicast to both CTAs.
 // The A and Bt halves of an operand stage share one "full" barrier (all
 // producers arrive) and one "empty" barrier (one commit). Every producer
 // arrives on the first operand stage of a packed stage before the second,
@@ -64,35 +73,54 @@ constexpr int KS = 128;          // k (bits) per operand stage
 constexpr int KP = TC_PACKED_BITS;  // k (bits) per packed (TMA) stage
 constexpr int SUB = KP / KS;     // operand stages per packed stage
 constexpr int MMA_K = 32;        // k per tcgen05.mma for 8-bit operands
-constexpr int PSTAGES = 4;       // packed ring depth (shared)
-constexpr int ESTAGES = 4;       // operand ring depth (Bt in shared, A in TMEM)
-// 22 warps: an SM sub-partition (16 K registers) holds at most six of them,
-// which caps registers at 80 per thread.
-constexpr int BEXP_WARPS = 8;    // warps 0..7
-constexpr int AEXP_WARP0 = 8;    // warps 8..15: two per TMEM lane quarter, alternate stages
-constexpr int EPI_WARP0 = 16;    // warps 16..19 (warp % 4 = TMEM lane quarter)
-constexpr int TMA_WARP = 20;
-constexpr int MMA_WARP = 21;
-constexpr int THREADS = 22 * 32;
+// 18 warps: an SM sub-partition (16 K registers) holds at most five of
+// them, which leaves 96 registers per thread (the A expansion keeps 64
+// output words live for one wide TMEM store).
+constexpr int BEXP_WARPS = 4;    // warps 0..3
+constexpr int AEXP_WARP0 = 4;    // warps 4..11: two per TMEM lane quarter, alternate stages
+constexpr int EPI_WARP0 = 12;    // warps 12..15 (warp % 4 = TMEM lane quarter)
+constexpr int TMA_WARP = 16;
+constexpr int MMA_WARP = 17;
+constexpr int THREADS = 18 * 32;
+static_assert(AEXP_WARP0 % 4 == 0 && EPI_WARP0 % 4 == 0, "warp % 4 selects the TMEM lane quarter");
 constexpr int GROUP_M = 16;      // tile raster: 16 row-tiles per group
 
-constexpr int PA_BYTES = BM * KP / 8;    // 4 KB packed A per packed stage
-constexpr int PB_BYTES = BN * KP / 8;    // 8 KB packed Bt per packed stage
-constexpr int EB_BYTES = BN * KS;        // 32 KB expanded Bt per operand stage
 constexpr int ACC_COL = 0;               // accumulator: TMEM columns [0, BN)
 constexpr int A_COL = BN;                // A ring: columns [BN, BN + ESTAGES * KS / 4)
 constexpr int A_STAGE_COLS = KS / 4;     // 4 e4m3 per 32-bit column
 constexpr int TMEM_COLS = 512;
-static_assert(A_COL + ESTAGES * A_STAGE_COLS <= TMEM_COLS, "TMEM budget");
 
-constexpr int OFF_EB = 0;
-constexpr int OFF_PA = OFF_EB + ESTAGES * EB_BYTES;
-constexpr int OFF_PB = OFF_PA + PSTAGES * PA_BYTES;
-constexpr int OFF_BAR = OFF_PB + PSTAGES * PB_BYTES;
-// barriers: full_p[P], empty_p[P], full_e[E], empty_e[E], acc_full, acc_empty, drain
-constexpr int NBARS = 2 * PSTAGES + 2 * ESTAGES + 3;
-constexpr int OFF_TMEM_SLOT = OFF_BAR + NBARS * 8;
-constexpr int SMEM_BYTES = OFF_TMEM_SLOT + 16 + 1024;  // + alignment slack
+// Per-CTA shapes and shared-memory layout. A CTA always owns 128 rows of C
+// (its 128 TMEM lanes) and the matching 128 rows of A. A CTA on its own
+// (cta_group::1) also expands all 256 Bt rows of its 128 x 256 tile. In a
+// pair (a cluster of two CTAs on two SMs, cta_group::2, one 256 x 256 tile)
+// each CTA expands only its half of the Bt rows, and the pair's MMAs read
+// both halves: per SM, half the shared-memory traffic and a third less
+// expansion work for the same number of MACs.
+template <bool PAIR>
+struct Lay {
+    // ring depths: packed stages (shared) and operand stages (Bt in shared,
+    // A in TMEM); a pair's smaller operand stages leave room for deeper rings
+    static constexpr int PSTAGES = PAIR ? 6 : 4;
+    static constexpr int ESTAGES = PAIR ? 8 : 4;
+    // barriers: full_p[P], empty_p[P], full_e[E], empty_e[E], acc_full, acc_empty, drain
+    static constexpr int NBARS = 2 * PSTAGES + 2 * ESTAGES + 3;
+    static constexpr int TILE_M = PAIR ? 2 * BM : BM;  // rows of C per tile
+    static constexpr int BROWS = PAIR ? BN / 2 : BN;   // Bt rows held by one CTA
+    static constexpr int PA_BYTES = BM * KP / 8;       // 4 KB packed A per packed stage
+    static constexpr int PB_BYTES = BROWS * KP / 8;    // packed Bt per packed stage
+    static constexpr int EB_BYTES = BROWS * KS;        // expanded Bt per operand stage
+    static constexpr int OFF_EB = 0;
+    static constexpr int OFF_PA = OFF_EB + ESTAGES * EB_BYTES;
+    static constexpr int OFF_PB = OFF_PA + PSTAGES * PA_BYTES;
+    static constexpr int OFF_BAR = OFF_PB + PSTAGES * PB_BYTES;
+    static constexpr int OFF_TMEM_SLOT = OFF_BAR + NBARS * 8;
+    static constexpr int SMEM_BYTES = OFF_TMEM_SLOT + 16 + 1024;  // + alignment slack
+    static_assert(EB_BYTES % 1024 == 0, "swizzle atoms stay 1024-byte aligned");
+    static_assert(A_COL + ESTAGES * A_STAGE_COLS <= TMEM_COLS, "TMEM budget");
+    static_assert(ESTAGES % SUB == 0, "a packed stage's operand stages are adjacent in TMEM");
+    static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
+};
 
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s
 
@@ -146,9 +174,32 @@ __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, uint3
     }
 }
 
+// Arrive on the barrier at the same shared-memory offset in CTA `cta` of
+// the cluster. What the waiter goes on to use is this CTA's own shared
+// memory and TMEM, read by the pair's tensor cores; the writer orders it
+// with fence.proxy.async.shared::cta or tcgen05.fence before arriving, so a
+// CTA-scope arrive is enough (a cluster-scope release costs a memory barrier).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar, uint32_t cta) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(bar), "r"(cta));
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of both CTAs of the cluster (no thread may have exited).
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+
 __device__ __forceinline__ void fence_barrier_init() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -202,25 +253,74 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
 
 // Instruction descriptor for kind::f8f6f4: D format (1 = F32), A and B
 // format 0 (E4M3), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+template <int M>
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t dfmt) {
-    return (dfmt << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    return (dfmt << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// D (TMEM) += A (TMEM) x B (shared, descriptor).
+// D (TMEM) += A (TMEM) x B (shared, descriptor). PAIR: cta_group::2, issued
+// by the even CTA of the pair; A, B and D are the two CTAs' halves at the
+// same TMEM / shared-memory addresses.
+template <bool PAIR>
 __device__ __forceinline__ void mma_f8_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t db,
                                           uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "r"(tmem_a), "l"(db), "r"(idesc), "r"(accumulate)
-        : "memory");
+    if (PAIR)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "r"(tmem_a), "l"(db), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "r"(tmem_a), "l"(db), "r"(idesc), "r"(accumulate)
+            : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
+// Arrive on `bar` once every MMA this thread issued so far has completed.
+// PAIR: on the barrier at the same offset in each CTA of `mask`.
+template <bool PAIR>
+__device__ __forceinline__ void mma_commit(uint32_t bar, uint16_t mask = 3) {
+    if (PAIR)
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+            " [%0], %1;" ::"r"(bar),
+            "h"(mask)
+            : "memory");
+    else
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+            : "memory");
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void tmem_alloc(uint32_t slot) {
+    if (PAIR) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+}
+
+template <bool PAIR>
+__device__ __forceinline__ void tmem_dealloc(uint32_t tmem) {
+    if (PAIR)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
@@ -240,17 +340,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+// 32 lanes x 64 columns: one row per thread, 64 consecutive 32-bit columns
+// (both operand stages of a packed stage in one instruction; TMEM stores
+// share the tensor pipe's issue path with the MMAs, so fewer, wider ones).
+__device__ __forceinline__ void tmem_st64(uint32_t taddr, const uint32_t (&v)[64]) {
     asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], "
         "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
-        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, "
+        "%33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, "
+        "%49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63, %64};" ::"r"(
             taddr),
         "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
         "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
         "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]),
         "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]),
-        "r"(v[29]), "r"(v[30]), "r"(v[31])
+        "r"(v[29]), "r"(v[30]), "r"(v[31]), "r"(v[32]), "r"(v[33]), "r"(v[34]), "r"(v[35]),
+        "r"(v[36]), "r"(v[37]), "r"(v[38]), "r"(v[39]), "r"(v[40]), "r"(v[41]), "r"(v[42]),
+        "r"(v[43]), "r"(v[44]), "r"(v[45]), "r"(v[46]), "r"(v[47]), "r"(v[48]), "r"(v[49]),
+        "r"(v[50]), "r"(v[51]), "r"(v[52]), "r"(v[53]), "r"(v[54]), "r"(v[55]), "r"(v[56]),
+        "r"(v[57]), "r"(v[58]), "r"(v[59]), "r"(v[60]), "r"(v[61]), "r"(v[62]), "r"(v[63])
         : "memory");
 }
 
@@ -339,20 +448,31 @@ struct Tile {
     int m, n, nks, op, tm, tn, leaf;
 };
 
-template <bool BATCHED>
+// Scheduling unit: a CTA, or a CTA pair (consecutive blockIdx.x, one cluster).
+template <bool PAIR>
+__device__ __forceinline__ int unit_id() {
+    return PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+}
+template <bool PAIR>
+__device__ __forceinline__ int unit_count() {
+    return PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+}
+
+template <bool BATCHED, bool PAIR>
 __device__ __forceinline__ int tile_count(const Params& p) {
-    if (BATCHED) return p.cta_ptr[blockIdx.x + 1] - p.cta_ptr[blockIdx.x];
+    const int u = unit_id<PAIR>();
+    if (BATCHED) return p.cta_ptr[u + 1] - p.cta_ptr[u];
     int c = 0;
-    for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x) c++;
+    for (int t = u; t < p.total_tiles; t += unit_count<PAIR>()) c++;
     return c;
 }
 
-template <bool BATCHED>
+template <bool BATCHED, bool PAIR>
 __device__ __forceinline__ Tile tile_get(const Params& p, int idx, const CUtensorMap* tmA,
                                          const CUtensorMap* tmB) {
     Tile t;
     if (BATCHED) {
-        const TcWorkItem w = p.items[p.cta_ptr[blockIdx.x] + idx];
+        const TcWorkItem w = p.items[p.cta_ptr[unit_id<PAIR>()] + idx];
         const TcProblem* d = p.probs + w.prob;
         t.ma = &d->mapA;
         t.mb = &d->mapB;
@@ -366,7 +486,8 @@ __device__ __forceinline__ Tile tile_get(const Params& p, int idx, const CUtenso
         t.tn = w.tn;
         t.leaf = 0;
     } else {
-        const TileCoord c = tile_of(blockIdx.x + idx * gridDim.x, p.tiles_m, p.tiles_n);
+        const TileCoord c =
+            tile_of(unit_id<PAIR>() + idx * unit_count<PAIR>(), p.tiles_m, p.tiles_n);
         t.ma = tmA;
         t.mb = tmB;
         t.C = p.C + (int64_t)c.leaf * p.strideC;
@@ -382,20 +503,22 @@ __device__ __forceinline__ Tile tile_get(const Params& p, int idx, const CUtenso
     return t;
 }
 
-template <bool BATCHED>
+template <bool BATCHED, bool PAIR>
 __device__ __forceinline__ int tile_nks(const Params& p, int idx) {
-    if (BATCHED) return p.probs[p.items[p.cta_ptr[blockIdx.x] + idx].prob].nks;
+    if (BATCHED) return p.probs[p.items[p.cta_ptr[unit_id<PAIR>()] + idx].prob].nks;
     return p.nks;
 }
 
-template <bool BATCHED>
+template <bool BATCHED, bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const Params p) {
+    using LY = Lay<PAIR>;
+    constexpr int PSTAGES = LY::PSTAGES, ESTAGES = LY::ESTAGES;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar0 = sbase + OFF_BAR;
+    const uint32_t bar0 = sbase + LY::OFF_BAR;
     auto full_p = [&](int s) { return bar0 + 8u * s; };
     auto empty_p = [&](int s) { return bar0 + 8u * (PSTAGES + s); };
     auto full_e = [&](int s) { return bar0 + 8u * (2 * PSTAGES + s); };
@@ -403,9 +526,19 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t acc_full = bar0 + 8u * (2 * PSTAGES + 2 * ESTAGES);
     const uint32_t acc_empty = acc_full + 8u;
     const uint32_t drain_bar = acc_full + 16u;
-    uint32_t* tmem_slot = (uint32_t*)(smem + OFF_TMEM_SLOT);
+    uint32_t* tmem_slot = (uint32_t*)(smem + LY::OFF_TMEM_SLOT);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // In a pair, CTA 0 issues the MMAs and holds the barriers that gate them
+    // (full_e, acc_empty); both CTAs' producers and epilogues arrive there.
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    constexpr uint32_t CTAS = PAIR ? 2u : 1u;
+    auto arrive_leader = [&](uint32_t bar) {
+        if (PAIR)
+            mbar_arrive_cluster(bar, 0);
+        else
+            mbar_arrive(bar);
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < PSTAGES; s++) {
@@ -413,21 +546,15 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(empty_p(s), BEXP_WARPS + 4);  // 8 Bt warps + the 4 A warps of that stage
         }
         for (int s = 0; s < ESTAGES; s++) {
-            mbar_init(full_e(s), BEXP_WARPS + 4);  // 8 Bt warps + the 4 A warps of that stage
+            mbar_init(full_e(s), CTAS * (BEXP_WARPS + 4));  // per CTA: 8 Bt + 4 A warps
             mbar_init(empty_e(s), 1);
         }
         mbar_init(acc_full, 1);
-        mbar_init(acc_empty, 4);
+        mbar_init(acc_empty, CTAS * 4);
         mbar_init(drain_bar, 1);
         fence_barrier_init();
     }
-    if (warp == MMA_WARP) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    if (warp == MMA_WARP) tmem_alloc<PAIR>(smem_u32(tmem_slot));
     if (!BATCHED && warp == TMA_WARP && lane == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA))
                      : "memory");
@@ -436,13 +563,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
+    if (PAIR) cluster_sync();  // the peer's barriers exist before anything arrives on them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
     const int kchunk = p.kchunk;
-    const int my_tiles = tile_count<BATCHED>(p);
+    const int my_tiles = tile_count<BATCHED, PAIR>(p);
     int total_it = 0;  // operand stages this CTA runs
-    for (int i = 0; i < my_tiles; i++) total_it += tile_nks<BATCHED>(p, i);
+    for (int i = 0; i < my_tiles; i++) total_it += tile_nks<BATCHED, PAIR>(p, i);
 
     if (warp == TMA_WARP) {
         // ---------------------------------------------------- TMA producer
@@ -450,17 +578,19 @@ __global__ void __launch_bounds__(THREADS, 1)
             int pit = 0;  // packed stages issued
             bool ok = true;
             for (int i = 0; ok && i < my_tiles; i++) {
-                const Tile tc = tile_get<BATCHED>(p, i, &tmA, &tmB);
+                const Tile tc = tile_get<BATCHED, PAIR>(p, i, &tmA, &tmB);
+                const int arow = tc.tm * LY::TILE_M + (int)rank * BM;
+                const int brow = tc.tn * BN + (int)rank * LY::BROWS;
                 for (int kp = 0; kp < tc.nks / SUB; kp++, pit++) {
                     const int s = pit % PSTAGES;
                     if (!mbar_wait(empty_p(s), ((pit / PSTAGES) & 1) ^ 1, p.err)) {
                         ok = false;
                         break;
                     }
-                    mbar_arrive_tx(full_p(s), PA_BYTES + PB_BYTES);
-                    tma_load_3d(sbase + OFF_PA + s * PA_BYTES, tc.ma, kp * (KP / 64), tc.tm * BM,
+                    mbar_arrive_tx(full_p(s), LY::PA_BYTES + LY::PB_BYTES);
+                    tma_load_3d(sbase + LY::OFF_PA + s * LY::PA_BYTES, tc.ma, kp * (KP / 64), arow,
                                 tc.leaf, full_p(s));
-                    tma_load_3d(sbase + OFF_PB + s * PB_BYTES, tc.mb, kp * (KP / 64), tc.tn * BN,
+                    tma_load_3d(sbase + LY::OFF_PB + s * LY::PB_BYTES, tc.mb, kp * (KP / 64), brow,
                                 tc.leaf, full_p(s));
                 }
             }
@@ -472,7 +602,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else if (warp < BEXP_WARPS) {
         // ---------------------------------------------------- Bt expansion (shared)
-        // Per packed stage: 64 items of 4 rows x 8 packed words (both operand
+        // Per packed stage: items of 4 rows x 8 packed words (both operand
         // stages). Lane = (half h, row rr of the item, word wl of the half):
         // word w = 4h + wl of the row goes to operand stage 2*pit + h. A
         // quarter-warp then holds two adjacent rows (opposite parity) x 4 words
@@ -488,9 +618,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!mbar_wait(full_p(s), (pit / PSTAGES) & 1, p.err) ||
                 !mbar_wait(empty_e(se1), (((it0 + 1) / ESTAGES) & 1) ^ 1, p.err))
                 break;
-            constexpr int ITEMS = (BN / 4) / BEXP_WARPS;
-            const uint32_t* pb = reinterpret_cast<const uint32_t*>(smem + OFF_PB + s * PB_BYTES);
-            uint8_t* eb = smem + OFF_EB + (h ? se1 : se0) * EB_BYTES;
+            constexpr int ITEMS = (LY::BROWS / 4) / BEXP_WARPS;
+            const uint32_t* pb =
+                reinterpret_cast<const uint32_t*>(smem + LY::OFF_PB + s * LY::PB_BYTES);
+            uint8_t* eb = smem + LY::OFF_EB + (h ? se1 : se0) * LY::EB_BYTES;
             uint32_t x[ITEMS];
 #pragma unroll
             for (int q = 0; q < ITEMS; q++)
@@ -511,8 +642,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) {
-                mbar_arrive(full_e(se0));
-                mbar_arrive(full_e(se1));
+                arrive_leader(full_e(se0));
+                arrive_leader(full_e(se1));
             }
         }
     } else if (warp < EPI_WARP0) {
@@ -529,42 +660,42 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int se0 = it0 % ESTAGES, se1 = (it0 + 1) % ESTAGES;
             if (!mbar_wait(full_p(s), (pit / PSTAGES) & 1, p.err))
                 break;
-            const uint4* src = reinterpret_cast<const uint4*>(smem + OFF_PA + s * PA_BYTES +
-                                                              row * (KP / 8));
+            const uint4* src = reinterpret_cast<const uint4*>(smem + LY::OFF_PA +
+                                                              s * LY::PA_BYTES + row * (KP / 8));
             const uint4 xa = src[0], xb = src[1];
             __syncwarp();
             if (lane == 0) mbar_arrive(empty_p(s));
-            uint32_t y[32];
             if (!mbar_wait(empty_e(se1), (((it0 + 1) / ESTAGES) & 1) ^ 1, p.err)) break;
+            // se1 = se0 + 1: the two operand stages are adjacent column ranges
+            uint32_t y[64];
             spread8(xa.x, sp, y);
             spread8(xa.y, sp, y + 8);
             spread8(xa.z, sp, y + 16);
             spread8(xa.w, sp, y + 24);
-            tmem_st32(tmem + tlane + (uint32_t)(A_COL + se0 * A_STAGE_COLS), y);
-            spread8(xb.x, sp, y);
-            spread8(xb.y, sp, y + 8);
-            spread8(xb.z, sp, y + 16);
-            spread8(xb.w, sp, y + 24);
-            tmem_st32(tmem + tlane + (uint32_t)(A_COL + se1 * A_STAGE_COLS), y);
+            spread8(xb.x, sp, y + 32);
+            spread8(xb.y, sp, y + 40);
+            spread8(xb.z, sp, y + 48);
+            spread8(xb.w, sp, y + 56);
+            tmem_st64(tmem + tlane + (uint32_t)(A_COL + se0 * A_STAGE_COLS), y);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
-                mbar_arrive(full_e(se0));
-                mbar_arrive(full_e(se1));
+                arrive_leader(full_e(se0));
+                arrive_leader(full_e(se1));
             }
         }
     } else if (warp == MMA_WARP) {
         // ---------------------------------------------------- MMA issuer
-        if (lane == 0) {
-            constexpr uint32_t idesc = instr_desc(1u);
-            uint64_t db0[ESTAGES];
-#pragma unroll
-            for (int s = 0; s < ESTAGES; s++) db0[s] = smem_desc_sw128(sbase + OFF_EB + s * EB_BYTES);
+        if (lane == 0 && rank == 0) {
+            constexpr uint32_t idesc = instr_desc<LY::TILE_M>(1u);
+            // stage s's descriptor: the start-address field (bytes >> 4) moves by
+            // EB_BYTES >> 4 per stage; every stage lies below 256 KB, so no carry
+            const uint64_t db_base = smem_desc_sw128(sbase + LY::OFF_EB);
             int seg = 0, pit = 0;
             bool ok = true;
             for (int i = 0; ok && i < my_tiles; i++) {
-                const int nks = tile_nks<BATCHED>(p, i);
+                const int nks = tile_nks<BATCHED, PAIR>(p, i);
                 int kin = 0;
                 for (int ks = 0; ks < nks; ks += SUB, pit++) {
                     if (kin == 0) {
@@ -574,7 +705,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                         }
                     }
                     const int it0 = pit * SUB;
-                    if (!mbar_wait(full_e((it0 + 1) % ESTAGES), ((it0 + 1) / ESTAGES) & 1, p.err)) {
+                    if (!mbar_wait(full_e((it0 + 1) % ESTAGES), ((it0 + 1) / ESTAGES) & 1,
+                                         p.err)) {
                         ok = false;
                         break;
                     }
@@ -583,26 +715,23 @@ __global__ void __launch_bounds__(THREADS, 1)
                     for (int sub = 0; sub < SUB; sub++) {
                         const int se = (it0 + sub) % ESTAGES;
                         const uint32_t ta = tmem + (uint32_t)(A_COL + se * A_STAGE_COLS);
-                        uint64_t db = db0[0];
-#pragma unroll
-                        for (int s = 1; s < ESTAGES; s++)
-                            if (se == s) db = db0[s];
+                        const uint64_t db = db_base + (uint64_t)(se * (LY::EB_BYTES >> 4));
 #pragma unroll
                         for (int j = 0; j < KS / MMA_K; j++)
-                            mma_f8_ta(tmem + ACC_COL, ta + j * (MMA_K / 4), db + 2 * j, idesc,
-                                      (kin > 0 || sub > 0 || j > 0) ? 1u : 0u);
-                        mma_commit(empty_e(se));
+                            mma_f8_ta<PAIR>(tmem + ACC_COL, ta + j * (MMA_K / 4), db + 2 * j, idesc,
+                                            (kin > 0 || sub > 0 || j > 0) ? 1u : 0u);
+                        mma_commit<PAIR>(empty_e(se));
                     }
                     kin += SUB;
                     if (kin >= kchunk || ks + SUB >= nks) {
-                        mma_commit(acc_full);
+                        mma_commit<PAIR>(acc_full);
                         seg++;
                         kin = 0;
                     }
                 }
             }
             if (!ok) {  // wait (bounded) for every MMA this thread issued
-                mma_commit(drain_bar);
+                mma_commit<PAIR>(drain_bar, 1);
                 mbar_wait(drain_bar, 0, p.err);
             }
         }
@@ -613,7 +742,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         int seg = 0;
         bool ok = true;
         for (int i = 0; ok && i < my_tiles; i++) {
-            const Tile tc = tile_get<BATCHED>(p, i, &tmA, &tmB);
+            const Tile tc = tile_get<BATCHED, PAIR>(p, i, &tmA, &tmB);
             const int nseg = (tc.nks + kchunk - 1) / kchunk;
             const bool gf2 = tc.op == OP_GF2;
             uint32_t words[BN / 32];
@@ -636,10 +765,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(acc_empty);
+                if (lane == 0) arrive_leader(acc_empty);
             }
             if (!ok) break;
-            const int64_t row = (int64_t)tc.tm * BM + 32 * quarter + lane;
+            const int64_t row =
+                (int64_t)tc.tm * LY::TILE_M + (int64_t)rank * BM + 32 * quarter + lane;
             if (row < tc.m) {
                 uint64_t* crow = tc.C + row * tc.ldc;
                 const int64_t w0 = (int64_t)tc.tn * (BN / 64);
@@ -654,11 +784,12 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     tc_fence_before();
     __syncthreads();
+    // A pair leaves together: the peer's remote arrivals and the MMAs that
+    // read its shared memory and TMEM are over before either CTA frees TMEM.
+    if (PAIR) cluster_sync();
     if (warp == MMA_WARP) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TMEM_COLS)
-                     : "memory");
+        tmem_dealloc<PAIR>(tmem);
     }
 }
 
@@ -695,19 +826,67 @@ bool make_map(CUtensorMap* map, const uint64_t* base, int64_t kwords, int64_t ro
     return r == CUDA_SUCCESS;
 }
 
-template <bool BATCHED>
-cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const Params& prm, int grid,
+template <bool BATCHED, bool PAIR>
+cudaError_t set_smem_attr() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        err = cudaFuncSetAttribute(tc_nt_kernel<BATCHED, PAIR>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   Lay<PAIR>::SMEM_BYTES);
+    });
+    return err;
+}
+
+// CTA pairs that can be resident at once (clusters of two on one TPC).
+int pair_slots() {
+    static std::once_flag once;
+    static int slots = 0;
+    std::call_once(once, [] {
+        if (set_smem_attr<false, true>() != cudaSuccess) return;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * (unsigned)sm_count());
+        cfg.blockDim = dim3(THREADS);
+        cfg.dynamicSmemBytes = Lay<true>::SMEM_BYTES;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, tc_nt_kernel<false, true>, &cfg) == cudaSuccess)
+            slots = n;
+        else
+            (void)cudaGetLastError();
+    });
+    return slots;
+}
+
+// units: CTAs (single) or CTA pairs (PAIR) to launch.
+template <bool BATCHED, bool PAIR>
+cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const Params& prm, int units,
                       cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_nt_kernel<BATCHED>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr = true;
+    const cudaError_t e = set_smem_attr<BATCHED, PAIR>();
+    if (e != cudaSuccess) return e;
+    if (!PAIR) {
+        tc_nt_kernel<BATCHED, false><<<units, THREADS, Lay<false>::SMEM_BYTES, s>>>(ma, mb, prm);
+        return cudaGetLastError();
     }
-    tc_nt_kernel<BATCHED><<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, prm);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * (unsigned)units);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = Lay<PAIR>::SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tc_nt_kernel<BATCHED, PAIR>, ma, mb, prm);
 }
 
 Spread spread_factors() {
@@ -720,13 +899,16 @@ Spread spread_factors() {
 
 bool tc_path_available() { return device_cc() == 103 && encode_fn() != nullptr; }
 
+// SM pairs need cluster launches with both CTAs of a pair resident at once.
+bool tc_pair_available() { return tc_path_available() && pair_slots() > 0; }
+
 // Longest run of k stages accumulated before the counts are flushed from
 // TMEM: the e4m3 path reads parity through an FP32 value count * 2^-12,
 // exact while count < 2^23 (at most 65534 stages of 128); S32 needs none.
 int tc_kchunk_stages(int path, int nks) {
     // a multiple of the operand stages per packed stage (flushes happen between packed stages)
     const int cap = 65534;
-    if (path == BMM_PATH_TC_FP8) return nks < cap ? nks : cap;
+    if (path == BMM_PATH_TC_FP8 || path == BMM_PATH_TC_FP8_PAIR) return nks < cap ? nks : cap;
     return nks;
 }
 
@@ -734,15 +916,20 @@ bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int6
                           const uint64_t* Bt, int64_t ldb, int64_t strideB, uint64_t* C,
                           int64_t ldc, int64_t strideC, int64_t count, int64_t m, int64_t k,
                           int64_t n, cudaStream_t s) {
-    if (!tc_path_available() || path != BMM_PATH_TC_FP8) return BMM_ERR_UNSUPPORTED;
+    const bool pair = path == BMM_PATH_TC_FP8_PAIR;
+    if (!tc_path_available() || (path != BMM_PATH_TC_FP8 && !pair)) return BMM_ERR_UNSUPPORTED;
     if (k % KS || (lda & 1) || (ldb & 1) || (count > 1 && ((strideA & 1) || (strideB & 1))))
         return BMM_ERR_UNSUPPORTED;
     if (m <= 0 || n <= 0 || k <= 0 || count <= 0) return BMM_OK;
+    const int slots = pair ? pair_slots() : sm_count();
+    if (slots <= 0) return BMM_ERR_UNSUPPORTED;
     uint32_t* err = device_error_word();
     if (!err) return BMM_ERR_NOMEM;
+    const int tile_m = pair ? Lay<true>::TILE_M : Lay<false>::TILE_M;
+    const int brows = pair ? Lay<true>::BROWS : Lay<false>::BROWS;
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, k / 64, m, lda, count, strideA, BM) ||
-        !make_map(&mb, Bt, k / 64, n, ldb, count, strideB, BN))
+        !make_map(&mb, Bt, k / 64, n, ldb, count, strideB, brows))
         return BMM_ERR_CUDA;
     Params prm{};
     prm.C = C;
@@ -753,7 +940,7 @@ bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int6
     prm.nks = (int)((k + KP - 1) / KP) * SUB;  // whole packed stages; the tail is zero-filled
     prm.op = op;
     prm.kchunk = tc_kchunk_stages(path, prm.nks);
-    prm.tiles_m = (int)((m + BM - 1) / BM);
+    prm.tiles_m = (int)((m + tile_m - 1) / tile_m);
     prm.tiles_n = (int)((n + BN - 1) / BN);
     const int64_t total = (int64_t)prm.tiles_m * prm.tiles_n * count;
     if (total > 0x7fffffff) return BMM_ERR_UNSUPPORTED;
@@ -761,8 +948,9 @@ bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int6
     prm.err = err;
     prm.sp = spread_factors();
     TraceScope ts(BMM_PHASE_BASE, s);
-    const int grid = prm.total_tiles < sm_count() ? prm.total_tiles : sm_count();
-    const cudaError_t e = launch_tc<false>(ma, mb, prm, grid, s);
+    const int units = prm.total_tiles < slots ? prm.total_tiles : slots;
+    const cudaError_t e = pair ? launch_tc<false, true>(ma, mb, prm, units, s)
+                               : launch_tc<false, false>(ma, mb, prm, units, s);
     if (e != cudaSuccess) return cuda_fail(e);
     return BMM_OK;
 }
@@ -776,7 +964,7 @@ bool tc_make_problem(TcProblem* out, const uint64_t* A, int64_t lda, const uint6
                      int op) {
     if (k % KS || (lda & 1) || (ldb & 1)) return false;
     if (!make_map(&out->mapA, A, k / 64, m, lda, 1, 0, BM) ||
-        !make_map(&out->mapB, Bt, k / 64, n, ldb, 1, 0, BN))
+        !make_map(&out->mapB, Bt, k / 64, n, ldb, 1, 0, Lay<false>::BROWS))
         return false;
     out->C = C;
     out->ldc = ldc;
@@ -801,7 +989,7 @@ cudaError_t tc_launch_batched(const TcProblem* d_probs, const TcWorkItem* d_item
     CUtensorMap dummy;
     std::memset(&dummy, 0, sizeof(dummy));
     TraceScope ts(BMM_PHASE_BASE, s);
-    return launch_tc<true>(dummy, dummy, prm, grid, s);
+    return launch_tc<true, false>(dummy, dummy, prm, grid, s);
 }
 
 }  // namespace bmm

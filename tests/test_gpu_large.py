@@ -87,9 +87,10 @@ def test_config2_square32768_bench_launch_configuration():
 
 
 def test_config3_square65536_paths_agree():
-    """m = k = n = 65536, seed 3: the tensor-core and CUDA-core base cases give
-    bit-identical products (cubic), and both match the oracle's samples; the
-    planner's Strassen product matches too. GF(2) p = 1/2, Boolean p = 2^-8."""
+    """m = k = n = 65536, seed 3: the tensor-core base cases (one SM or an SM
+    pair per tile) and the CUDA-core base case give bit-identical products
+    (cubic), and match the oracle's samples; the planner's Strassen product
+    matches too. GF(2) p = 1/2, Boolean p = 2^-8."""
     n, seed = 65536, 3
     if not bmm.device_supported():
         pytest.skip("tensor-core path needs sm_103")
@@ -97,6 +98,9 @@ def test_config3_square65536_paths_agree():
         tc = run_product(op, n, seed, ids, p, path=bmm.PATH_TC_FP8, depth=0)
         pc = run_product(op, n, seed, ids, p, path=bmm.PATH_POPC, depth=0)
         assert (tc == pc).all(), f"tensor vs CUDA-core disagree (op={op})"
+        tp = run_product(op, n, seed, ids, p, path=bmm.PATH_TC_FP8_PAIR, depth=0)
+        assert (tp == tc).all(), f"SM-pair vs single-SM tensor paths disagree (op={op})"
+        del tp
         if op == bmm.GF2:
             st = run_product(op, n, seed, ids, p)
             assert (st == tc).all(), "Strassen vs cubic disagree"

@@ -23,7 +23,7 @@ OPS = {bmm.GF2: O.GF2, bmm.BOOL: O.BOOL}
 def paths():
     ps = [bmm.PATH_POPC]
     if bmm.device_supported():
-        ps.append(bmm.PATH_TC_FP8)
+        ps += [bmm.PATH_TC_FP8, bmm.PATH_TC_FP8_PAIR]
     return ps
 
 

@@ -15,20 +15,20 @@
 //               into a PSTAGES-deep shared ring (cp.async.bulk.tensor,
 //               mbarrier complete_tx). Each packed stage feeds two operand
 //               stages of 128 bits.
-//   warps 4-11  A expansion: one row per thread, 256 bits -> 256 e4m3
-//               bytes (both operand stages) written straight into TMEM with
-//               one tcgen05.st; two warps per TMEM lane quarter take
-//               alternate packed stages.
-//   warps 0-3   Bt expansion: each packed 32-bit word becomes 32 bytes of
-//               the K-major, 128-byte-swizzled canonical UMMA layout; a warp
-//               expands 4 whole rows of a packed stage at a time.
-//   warp 17     MMA issuer: per packed stage, one wait, then for each of its
-//               two operand stages 4 x tcgen05.mma (M=128, N=256, K=32; A
-//               from TMEM, B from shared memory) into the TMEM accumulator
-//               and one commit that frees that operand stage.
-//   warps 12-15 epilogue: tcgen05.ld 32 lanes x 32 columns at a time, parity
+//   Bt expansion (8 warps; 4 in a pair): each packed 32-bit word becomes
+//               32 bytes of the K-major, 128-byte-swizzled canonical UMMA
+//               layout; a warp expands 4 whole rows of a packed stage at a
+//               time.
+//   A expansion (4 warps, one per TMEM lane quarter): one row per thread,
+//               every packed stage: 256 bits -> 256 e4m3 bytes (both operand
+//               stages) written straight into TMEM with one tcgen05.st.
+//   epilogue (4 warps; 8 in a pair, two per lane quarter splitting the
+//               columns): tcgen05.ld 32 lanes x 32 columns at a time, parity
 //               or non-zero test, bits packed in registers with a shallow
 //               tree (one row per thread) and stored as 64-bit words.
+//   warp 17     MMA issuer: per packed stage, 2 x 4 tcgen05.mma (M=128,
+//               N=256, K=32; A from TMEM, B from shared memory) into the TMEM
+//               accumulator and one commit that frees the operand slot.
 // SM pairs (PAIR): two CTAs of a cluster on two SMs share one 256 x 256 tile
 // through tcgen05.mma.cta_group::2 (M=256). Each CTA expands its own 128 rows
 // of A into its TMEM and its own 128 of the tile's 256 Bt rows into its
@@ -37,15 +37,16 @@
 // barriers (operand stage full, accumulator empty) live in the even CTA and
 // both CTAs' producers and epilogues arrive there; the commits that free an
 // operand stage or publish the accumulator are multicast to both CTAs.
-// The A and Bt halves of an operand stage share one "full" barrier (all
-// producers arrive) and one "empty" barrier (one commit). Every producer
-// arrives on the first operand stage of a packed stage before the second,
-// and commits complete in order, so waiting for the second stage's barrier
-// covers both: each role checks one barrier per packed stage (a check costs
-// ~190 cycles of latency, even when the phase is already complete). Keeping A in TMEM
-// means shared memory carries only Bt (written once, read once by the tensor
-// core). Long k is flushed from TMEM in chunks of `kchunk` stages (the
-// epilogue folds parities / ORs across chunks).
+// The two operand stages a packed stage fills form one slot with one "full"
+// barrier (every producer arrives) and one "empty" barrier (one commit).
+// Every producer handles every packed stage in order, so the MMA issuer's
+// wait on a slot covers the slots before it too: with four or more slots it
+// checks one barrier per two packed stages (a check costs ~190 cycles of
+// latency, even when the phase is already complete). TMEM stores share the tensor pipe's issue path
+// with the MMAs, so A goes in with one wide store per packed stage. Keeping
+// A in TMEM means shared memory carries only Bt (written once, read once by
+// the tensor core). Long k is flushed from TMEM in chunks of `kchunk` stages
+// (the epilogue folds parities / ORs across chunks).
 //
 // Within every 32-element group of k the expansion permutes k (byte t of
 // output word j holds bit 8t + j of the packed word); A and Bt use the same
@@ -75,14 +76,13 @@ constexpr int SUB = KP / KS;     // operand stages per packed stage
 constexpr int MMA_K = 32;        // k per tcgen05.mma for 8-bit operands
 // 18 warps: an SM sub-partition (16 K registers) holds at most five of
 // them, which leaves 96 registers per thread (the A expansion keeps 64
-// output words live for one wide TMEM store).
-constexpr int BEXP_WARPS = 4;    // warps 0..3
-constexpr int AEXP_WARP0 = 4;    // warps 4..11: two per TMEM lane quarter, alternate stages
-constexpr int EPI_WARP0 = 12;    // warps 12..15 (warp % 4 = TMEM lane quarter)
+// output words live for one wide TMEM store). Warps 0..15 are split between
+// Bt expansion, A expansion (one warp per TMEM lane quarter) and the
+// epilogue as the layout below gives; then the TMA and MMA warps.
+constexpr int AEXP_WARPS = 4;
 constexpr int TMA_WARP = 16;
 constexpr int MMA_WARP = 17;
 constexpr int THREADS = 18 * 32;
-static_assert(AEXP_WARP0 % 4 == 0 && EPI_WARP0 % 4 == 0, "warp % 4 selects the TMEM lane quarter");
 constexpr int GROUP_M = 16;      // tile raster: 16 row-tiles per group
 
 constexpr int ACC_COL = 0;               // accumulator: TMEM columns [0, BN)
@@ -103,8 +103,22 @@ struct Lay {
     // A in TMEM); a pair's smaller operand stages leave room for deeper rings
     static constexpr int PSTAGES = PAIR ? 6 : 4;
     static constexpr int ESTAGES = PAIR ? 8 : 4;
-    // barriers: full_p[P], empty_p[P], full_e[E], empty_e[E], acc_full, acc_empty, drain
-    static constexpr int NBARS = 2 * PSTAGES + 2 * ESTAGES + 3;
+    // operand slots: the two operand stages one packed stage fills
+    static constexpr int OSLOTS = ESTAGES / SUB;
+    // packed stages the MMA issuer covers with one wait (needs more slots
+    // than that, or the producers cannot run ahead)
+    static constexpr int WAITG = OSLOTS >= 4 ? 2 : 1;
+    // barriers: full_p[P], empty_p[P], full_o[O], empty_o[O], acc_full, acc_empty, drain
+    static constexpr int NBARS = 2 * PSTAGES + 2 * OSLOTS + 3;
+    // warps: Bt expansion [0, BEXP_WARPS), A expansion [AEXP_WARP0, +4),
+    // epilogue [EPI_WARP0, TMA_WARP). A CTA alone has twice the Bt rows, a
+    // pair's MMA issuer gains most from a short accumulator drain.
+    static constexpr int BEXP_WARPS = PAIR ? 4 : 8;
+    static constexpr int AEXP_WARP0 = BEXP_WARPS;
+    static constexpr int EPI_WARP0 = AEXP_WARP0 + AEXP_WARPS;
+    static constexpr int EPI_WARPS = TMA_WARP - EPI_WARP0;
+    static_assert(AEXP_WARP0 % 4 == 0 && EPI_WARP0 % 4 == 0 && EPI_WARPS % 4 == 0,
+                  "warp % 4 is the TMEM lane quarter");
     static constexpr int TILE_M = PAIR ? 2 * BM : BM;  // rows of C per tile
     static constexpr int BROWS = PAIR ? BN / 2 : BN;   // Bt rows held by one CTA
     static constexpr int PA_BYTES = BM * KP / 8;       // 4 KB packed A per packed stage
@@ -514,23 +528,25 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const Params p) {
     using LY = Lay<PAIR>;
-    constexpr int PSTAGES = LY::PSTAGES, ESTAGES = LY::ESTAGES;
+    constexpr int PSTAGES = LY::PSTAGES, OSLOTS = LY::OSLOTS;
+    constexpr int BEXP_WARPS = LY::BEXP_WARPS, EPI_WARP0 = LY::EPI_WARP0,
+                  EPI_WARPS = LY::EPI_WARPS;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
     const uint32_t bar0 = sbase + LY::OFF_BAR;
     auto full_p = [&](int s) { return bar0 + 8u * s; };
     auto empty_p = [&](int s) { return bar0 + 8u * (PSTAGES + s); };
-    auto full_e = [&](int s) { return bar0 + 8u * (2 * PSTAGES + s); };
-    auto empty_e = [&](int s) { return bar0 + 8u * (2 * PSTAGES + ESTAGES + s); };
-    const uint32_t acc_full = bar0 + 8u * (2 * PSTAGES + 2 * ESTAGES);
+    auto full_o = [&](int q) { return bar0 + 8u * (2 * PSTAGES + q); };
+    auto empty_o = [&](int q) { return bar0 + 8u * (2 * PSTAGES + OSLOTS + q); };
+    const uint32_t acc_full = bar0 + 8u * (2 * PSTAGES + 2 * OSLOTS);
     const uint32_t acc_empty = acc_full + 8u;
     const uint32_t drain_bar = acc_full + 16u;
     uint32_t* tmem_slot = (uint32_t*)(smem + LY::OFF_TMEM_SLOT);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // In a pair, CTA 0 issues the MMAs and holds the barriers that gate them
-    // (full_e, acc_empty); both CTAs' producers and epilogues arrive there.
+    // (full_o, acc_empty); both CTAs' producers and epilogues arrive there.
     const uint32_t rank = PAIR ? cluster_rank() : 0u;
     constexpr uint32_t CTAS = PAIR ? 2u : 1u;
     auto arrive_leader = [&](uint32_t bar) {
@@ -543,14 +559,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < PSTAGES; s++) {
             mbar_init(full_p(s), 1);
-            mbar_init(empty_p(s), BEXP_WARPS + 4);  // 8 Bt warps + the 4 A warps of that stage
+            mbar_init(empty_p(s), BEXP_WARPS + AEXP_WARPS);  // every expansion warp reads every stage
         }
-        for (int s = 0; s < ESTAGES; s++) {
-            mbar_init(full_e(s), CTAS * (BEXP_WARPS + 4));  // per CTA: 8 Bt + 4 A warps
-            mbar_init(empty_e(s), 1);
+        for (int q = 0; q < OSLOTS; q++) {
+            mbar_init(full_o(q), CTAS * (BEXP_WARPS + AEXP_WARPS));
+            mbar_init(empty_o(q), 1);
         }
         mbar_init(acc_full, 1);
-        mbar_init(acc_empty, CTAS * 4);
+        mbar_init(acc_empty, CTAS * EPI_WARPS);
         mbar_init(drain_bar, 1);
         fence_barrier_init();
     }
@@ -569,8 +585,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     const int kchunk = p.kchunk;
     const int my_tiles = tile_count<BATCHED, PAIR>(p);
-    int total_it = 0;  // operand stages this CTA runs
-    for (int i = 0; i < my_tiles; i++) total_it += tile_nks<BATCHED, PAIR>(p, i);
+    int total_pit = 0;  // packed stages this CTA runs
+    for (int i = 0; i < my_tiles; i++) total_pit += tile_nks<BATCHED, PAIR>(p, i) / SUB;
 
     if (warp == TMA_WARP) {
         // ---------------------------------------------------- TMA producer
@@ -604,36 +620,35 @@ __global__ void __launch_bounds__(THREADS, 1)
         // ---------------------------------------------------- Bt expansion (shared)
         // Per packed stage: items of 4 rows x 8 packed words (both operand
         // stages). Lane = (half h, row rr of the item, word wl of the half):
-        // word w = 4h + wl of the row goes to operand stage 2*pit + h. A
-        // quarter-warp then holds two adjacent rows (opposite parity) x 4 words
-        // of one half, whose swizzled 16-byte chunks are 8 distinct bank groups.
+        // word w = 4h + wl of the row goes to operand stage 2q + h of slot q.
+        // A quarter-warp then holds two adjacent rows (opposite parity) x 4
+        // words of one half, whose swizzled 16-byte chunks are 8 distinct bank
+        // groups.
         const int h = lane >> 4, rr = (lane >> 2) & 3, wl = lane & 3;
         const Spread sp = p.sp;
-        const int total_pit = total_it / SUB;
         static_assert(SUB == 2, "a packed stage feeds two operand stages");
         for (int pit = 0; pit < total_pit; pit++) {
             const int s = pit % PSTAGES;
-            const int it0 = pit * SUB;
-            const int se0 = it0 % ESTAGES, se1 = (it0 + 1) % ESTAGES;
+            const int q = pit % OSLOTS;
             if (!mbar_wait(full_p(s), (pit / PSTAGES) & 1, p.err) ||
-                !mbar_wait(empty_e(se1), (((it0 + 1) / ESTAGES) & 1) ^ 1, p.err))
+                !mbar_wait(empty_o(q), ((pit / OSLOTS) & 1) ^ 1, p.err))
                 break;
             constexpr int ITEMS = (LY::BROWS / 4) / BEXP_WARPS;
             const uint32_t* pb =
                 reinterpret_cast<const uint32_t*>(smem + LY::OFF_PB + s * LY::PB_BYTES);
-            uint8_t* eb = smem + LY::OFF_EB + (h ? se1 : se0) * LY::EB_BYTES;
+            uint8_t* eb = smem + LY::OFF_EB + (2 * q + h) * LY::EB_BYTES;
             uint32_t x[ITEMS];
 #pragma unroll
-            for (int q = 0; q < ITEMS; q++)
-                x[q] = pb[((warp + BEXP_WARPS * q) * 4 + rr) * 8 + 4 * h + wl];
+            for (int i = 0; i < ITEMS; i++)
+                x[i] = pb[((warp + BEXP_WARPS * i) * 4 + rr) * 8 + 4 * h + wl];
             __syncwarp();
             if (lane == 0) mbar_arrive(empty_p(s));
 #pragma unroll
-            for (int q = 0; q < ITEMS; q++) {
-                const int row = (warp + BEXP_WARPS * q) * 4 + rr;
+            for (int i = 0; i < ITEMS; i++) {
+                const int row = (warp + BEXP_WARPS * i) * 4 + rr;
                 uint8_t* rowp = eb + row * 128;
                 uint32_t y[8];
-                spread8(x[q], sp, y);
+                spread8(x[i], sp, y);
                 *reinterpret_cast<uint4*>(rowp + (((2 * wl) ^ (row & 7)) * 16)) =
                     make_uint4(y[0], y[1], y[2], y[3]);
                 *reinterpret_cast<uint4*>(rowp + (((2 * wl + 1) ^ (row & 7)) * 16)) =
@@ -641,32 +656,27 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             fence_proxy_async();
             __syncwarp();
-            if (lane == 0) {
-                arrive_leader(full_e(se0));
-                arrive_leader(full_e(se1));
-            }
+            if (lane == 0) arrive_leader(full_o(q));
         }
     } else if (warp < EPI_WARP0) {
         // ---------------------------------------------------- A expansion (TMEM)
+        // One warp per TMEM lane quarter, one row per thread, every packed
+        // stage: 256 bits -> 256 e4m3 bytes = both operand stages of the
+        // slot, adjacent TMEM columns, one store.
         const int quarter = warp & 3;
-        const int parity = (warp - AEXP_WARP0) >> 2;  // this warp takes packed stages pit % 2 == parity
         const int row = 32 * quarter + lane;
         const Spread sp = p.sp;
         const uint32_t tlane = (uint32_t)(32 * quarter) << 16;
-        const int total_pit = total_it / SUB;
-        for (int pit = parity; pit < total_pit; pit += 2) {
+        for (int pit = 0; pit < total_pit; pit++) {
             const int s = pit % PSTAGES;
-            const int it0 = pit * SUB;
-            const int se0 = it0 % ESTAGES, se1 = (it0 + 1) % ESTAGES;
-            if (!mbar_wait(full_p(s), (pit / PSTAGES) & 1, p.err))
-                break;
+            const int q = pit % OSLOTS;
+            if (!mbar_wait(full_p(s), (pit / PSTAGES) & 1, p.err)) break;
             const uint4* src = reinterpret_cast<const uint4*>(smem + LY::OFF_PA +
                                                               s * LY::PA_BYTES + row * (KP / 8));
             const uint4 xa = src[0], xb = src[1];
             __syncwarp();
             if (lane == 0) mbar_arrive(empty_p(s));
-            if (!mbar_wait(empty_e(se1), (((it0 + 1) / ESTAGES) & 1) ^ 1, p.err)) break;
-            // se1 = se0 + 1: the two operand stages are adjacent column ranges
+            if (!mbar_wait(empty_o(q), ((pit / OSLOTS) & 1) ^ 1, p.err)) break;
             uint32_t y[64];
             spread8(xa.x, sp, y);
             spread8(xa.y, sp, y + 8);
@@ -676,21 +686,19 @@ __global__ void __launch_bounds__(THREADS, 1)
             spread8(xb.y, sp, y + 40);
             spread8(xb.z, sp, y + 48);
             spread8(xb.w, sp, y + 56);
-            tmem_st64(tmem + tlane + (uint32_t)(A_COL + se0 * A_STAGE_COLS), y);
+            tmem_st64(tmem + tlane + (uint32_t)(A_COL + 2 * q * A_STAGE_COLS), y);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) {
-                arrive_leader(full_e(se0));
-                arrive_leader(full_e(se1));
-            }
+            if (lane == 0) arrive_leader(full_o(q));
         }
     } else if (warp == MMA_WARP) {
         // ---------------------------------------------------- MMA issuer
         if (lane == 0 && rank == 0) {
             constexpr uint32_t idesc = instr_desc<LY::TILE_M>(1u);
-            // stage s's descriptor: the start-address field (bytes >> 4) moves by
-            // EB_BYTES >> 4 per stage; every stage lies below 256 KB, so no carry
+            // operand stage e's descriptor: the start-address field (bytes >> 4)
+            // moves by EB_BYTES >> 4 per stage; every stage lies below 256 KB,
+            // so no carry
             const uint64_t db_base = smem_desc_sw128(sbase + LY::OFF_EB);
             int seg = 0, pit = 0;
             bool ok = true;
@@ -704,24 +712,29 @@ __global__ void __launch_bounds__(THREADS, 1)
                             break;
                         }
                     }
-                    const int it0 = pit * SUB;
-                    if (!mbar_wait(full_e((it0 + 1) % ESTAGES), ((it0 + 1) / ESTAGES) & 1,
-                                         p.err)) {
-                        ok = false;
-                        break;
+                    // Every producer fills the slots in order, so one wait on
+                    // the last of WAITG consecutive slots covers them all.
+                    if (pit % LY::WAITG == 0) {
+                        const int w = pit + LY::WAITG - 1 < total_pit ? pit + LY::WAITG - 1
+                                                                      : total_pit - 1;
+                        if (!mbar_wait(full_o(w % OSLOTS), (w / OSLOTS) & 1, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
                     }
-                    tc_fence_after();
+                    const int q = pit % OSLOTS;
 #pragma unroll
                     for (int sub = 0; sub < SUB; sub++) {
-                        const int se = (it0 + sub) % ESTAGES;
-                        const uint32_t ta = tmem + (uint32_t)(A_COL + se * A_STAGE_COLS);
-                        const uint64_t db = db_base + (uint64_t)(se * (LY::EB_BYTES >> 4));
+                        const int e = 2 * q + sub;
+                        const uint32_t ta = tmem + (uint32_t)(A_COL + e * A_STAGE_COLS);
+                        const uint64_t db = db_base + (uint64_t)(e * (LY::EB_BYTES >> 4));
 #pragma unroll
                         for (int j = 0; j < KS / MMA_K; j++)
                             mma_f8_ta<PAIR>(tmem + ACC_COL, ta + j * (MMA_K / 4), db + 2 * j, idesc,
                                             (kin > 0 || sub > 0 || j > 0) ? 1u : 0u);
-                        mma_commit<PAIR>(empty_e(se));
                     }
+                    mma_commit<PAIR>(empty_o(q));
                     kin += SUB;
                     if (kin >= kchunk || ks + SUB >= nks) {
                         mma_commit<PAIR>(acc_full);
@@ -737,17 +750,20 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else if (warp < TMA_WARP) {
         // ---------------------------------------------------- epilogue
+        // EPI_WARPS / 4 warps per TMEM lane quarter, splitting the columns.
         const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+        const int chalf = (warp - EPI_WARP0) >> 2;
         const uint32_t tlane = (uint32_t)(32 * quarter) << 16;
+        constexpr int CW = BN / (EPI_WARPS / 4) / 32;  // 32-column chunks per warp
         int seg = 0;
         bool ok = true;
         for (int i = 0; ok && i < my_tiles; i++) {
             const Tile tc = tile_get<BATCHED, PAIR>(p, i, &tmA, &tmB);
             const int nseg = (tc.nks + kchunk - 1) / kchunk;
             const bool gf2 = tc.op == OP_GF2;
-            uint32_t words[BN / 32];
+            uint32_t words[CW];
 #pragma unroll
-            for (int c = 0; c < BN / 32; c++) words[c] = 0u;
+            for (int c = 0; c < CW; c++) words[c] = 0u;
             for (int g = 0; g < nseg; g++, seg++) {
                 if (!mbar_wait(acc_full, seg & 1, p.err)) {
                     ok = false;
@@ -755,9 +771,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 tc_fence_after();
 #pragma unroll 2
-                for (int c = 0; c < BN / 32; c++) {
+                for (int c = 0; c < CW; c++) {
                     uint32_t v[32];
-                    tmem_ld32(tmem + tlane + (uint32_t)(ACC_COL + 32 * c), v);
+                    tmem_ld32(tmem + tlane + (uint32_t)(ACC_COL + 32 * (CW * chalf + c)), v);
                     if (gf2)
                         words[c] ^= pack_bits<OP_GF2>(v);
                     else
@@ -772,10 +788,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                 (int64_t)tc.tm * LY::TILE_M + (int64_t)rank * BM + 32 * quarter + lane;
             if (row < tc.m) {
                 uint64_t* crow = tc.C + row * tc.ldc;
-                const int64_t w0 = (int64_t)tc.tn * (BN / 64);
+                const int64_t w0 = (int64_t)tc.tn * (BN / 64) + chalf * (CW / 2);
                 const int64_t nw = tc.n / 64;
 #pragma unroll
-                for (int c = 0; c < BN / 64; c++)
+                for (int c = 0; c < CW / 2; c++)
                     if (w0 + c < nw)
                         crow[w0 + c] = (uint64_t)words[2 * c] | ((uint64_t)words[2 * c + 1] << 32);
             }

@@ -2,9 +2,9 @@
 //
 // A plan is built once on the host: per-problem TMA maps over A (or a copy of
 // A with an even row pitch) and over the transposed B, the work list of all
-// 128 x 256 output tiles, and a longest-processing-time-first assignment of
-// the tiles to one CTA per SM (each tile costs its k stages plus a fixed
-// epilogue share). Running a plan only launches kernels: one batched bit
+// 256 x 256 output tiles (128 x 256 where SM pairs are unavailable), and a
+// longest-processing-time-first assignment of the tiles to the resident CTA
+// pairs (or CTAs); each tile costs its k stages plus a fixed epilogue share. Running a plan only launches kernels: one batched bit
 // transpose of every B, one pass that pads rows whose k/64 word count is odd,
 // and one persistent launch of the tensor-core base case that walks each
 // CTA's list. Nothing in a run allocates or synchronises, so a run can be
@@ -68,6 +68,7 @@ struct bmm_batched_plan_s {
     int device = 0;
     int count = 0;
     bool tc = false;
+    bool pair = false;  // SM pairs: 256-row tiles, one work list per CTA pair
     // problem list (host)
     std::vector<int> op;
     std::vector<const uint64_t*> A, B;
@@ -94,6 +95,9 @@ namespace {
 bmm_status plan_build(bmm_batched_plan_s* P) {
     const int count = P->count;
     P->tc = tc_path_available();
+    const int pair_slots = P->tc ? tc_pair_slots() : 0;
+    P->pair = pair_slots > 0;
+    const int tile_m = P->pair ? 2 * TC_TILE_M : TC_TILE_M;
     // sizes of every device array
     std::vector<uint64_t> bt_off(count), ap_off(count, 0);
     P->kp.resize(count);
@@ -113,14 +117,14 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
     // tiles and their LPT assignment
     std::vector<TcWorkItem> items;
     for (int i = 0; i < count; i++) {
-        const int tm_n = (int)((P->m[i] + TC_TILE_M - 1) / TC_TILE_M);
+        const int tm_n = (int)((P->m[i] + tile_m - 1) / tile_m);
         const int tn_n = (int)((P->n[i] + TC_TILE_N - 1) / TC_TILE_N);
         const int nks = (int)((P->k[i] + TC_PACKED_BITS - 1) / TC_PACKED_BITS) * 2;
         for (int a = 0; a < tm_n; a++)
             for (int b = 0; b < tn_n; b++) items.push_back({i, a, b, nks + EPI_COST});
     }
-    const int sms = sm_count();
-    const int grid = (int)std::min<int64_t>((int64_t)items.size(), sms);
+    const int slots = P->pair ? pair_slots : sm_count();
+    const int grid = (int)std::min<int64_t>((int64_t)items.size(), slots);  // work units
     std::stable_sort(items.begin(), items.end(),
                      [](const TcWorkItem& x, const TcWorkItem& y) { return x.cost > y.cost; });
     std::vector<std::vector<TcWorkItem>> per(grid);
@@ -186,7 +190,7 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
         if (P->tc) {
             const int64_t kpad = P->kp[i] * 64;
             if (!tc_make_problem(&probs[i], Aop, lda, Bt, P->kp[i], P->C[i], P->n[i] / 64, P->m[i],
-                                 kpad, P->n[i], P->op[i]))
+                                 kpad, P->n[i], P->op[i], P->pair))
                 return BMM_ERR_CUDA;
         }
         tjobs[i] = {P->B[i], Bt, P->n[i] / 64, P->kp[i], P->k[i], P->n[i]};
@@ -229,7 +233,7 @@ bmm_status plan_run(bmm_batched_plan_s* P, cudaStream_t s) {
         BMM_CUDA_TRY(cudaGetLastError());
     }
     if (P->tc) {
-        BMM_CUDA_TRY(tc_launch_batched(P->d_probs, P->d_items, P->d_cta_ptr, P->grid, s));
+        BMM_CUDA_TRY(tc_launch_batched(P->d_probs, P->d_items, P->d_cta_ptr, P->grid, P->pair, s));
         return BMM_OK;
     }
     // without tensor cores: the CUDA-core base case, one launch per problem

@@ -975,12 +975,15 @@ bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int6
 
 namespace bmm {
 
+int tc_pair_slots() { return tc_path_available() ? pair_slots() : 0; }
+
 bool tc_make_problem(TcProblem* out, const uint64_t* A, int64_t lda, const uint64_t* Bt,
                      int64_t ldb, uint64_t* C, int64_t ldc, int64_t m, int64_t k, int64_t n,
-                     int op) {
+                     int op, bool pair) {
     if (k % KS || (lda & 1) || (ldb & 1)) return false;
     if (!make_map(&out->mapA, A, k / 64, m, lda, 1, 0, BM) ||
-        !make_map(&out->mapB, Bt, k / 64, n, ldb, 1, 0, Lay<false>::BROWS))
+        !make_map(&out->mapB, Bt, k / 64, n, ldb, 1, 0,
+                  pair ? Lay<true>::BROWS : Lay<false>::BROWS))
         return false;
     out->C = C;
     out->ldc = ldc;
@@ -992,20 +995,21 @@ bool tc_make_problem(TcProblem* out, const uint64_t* A, int64_t lda, const uint6
 }
 
 cudaError_t tc_launch_batched(const TcProblem* d_probs, const TcWorkItem* d_items,
-                              const int32_t* d_cta_ptr, int grid, cudaStream_t s) {
+                              const int32_t* d_unit_ptr, int units, bool pair, cudaStream_t s) {
     uint32_t* err = device_error_word();
     if (!err) return cudaErrorMemoryAllocation;
     Params prm{};
     prm.probs = d_probs;
     prm.items = d_items;
-    prm.cta_ptr = d_cta_ptr;
+    prm.cta_ptr = d_unit_ptr;
     prm.kchunk = 65534;
     prm.err = err;
     prm.sp = spread_factors();
     CUtensorMap dummy;
     std::memset(&dummy, 0, sizeof(dummy));
     TraceScope ts(BMM_PHASE_BASE, s);
-    return launch_tc<true, false>(dummy, dummy, prm, grid, s);
+    return pair ? launch_tc<true, true>(dummy, dummy, prm, units, s)
+                : launch_tc<true, false>(dummy, dummy, prm, units, s);
 }
 
 }  // namespace bmm

@@ -116,6 +116,37 @@ typedef struct {
 bmm_status bmm_plan(int32_t op, int64_t m, int64_t k, int64_t n, const bmm_opts *opts,
                     bmm_plan_info *info);
 
+/* Autotuner (Sec. 3.17: once memory capacity has fixed what it must, the few
+ * remaining parameter choices are made by measurement). Times the candidate
+ * base-case paths (tensor cores on SM pairs or single SMs where available,
+ * CUDA cores) and, for the binary product (op 0), every Strassen depth 0..4
+ * the sizes allow with leaves of at least 256 bits a side, and records the
+ * fastest (path, depth) for (op, m, k, n) on the current device; products
+ * whose options leave both path and depth to the library (bmm_gf2, bmm_bool,
+ * or bmm_opts_default) then use it. The depth-first level count stays with
+ * the planner's memory rule. Work is issued on `stream` with scratch of its
+ * own (stream-ordered; operands are synthetic), and the call synchronises it.
+ * A candidate is timed as a whole product when the product is small (its
+ * operands and scratch use at most a quarter of free memory and the cubic
+ * product would take under ~0.1 s); otherwise its leaf products are timed on
+ * a leaf-shaped proxy of at most 16384 bits a side, scaled to the leaf count
+ * and size, and its streaming passes are charged plan bytes at the measured
+ * device copy bandwidth. flags: BMM_TUNE_MODEL forces the second way.
+ * Errors: BMM_ERR_INVALID for bad op or sizes (as for the products),
+ * BMM_ERR_NOMEM if scratch cannot be had. */
+#define BMM_TUNE_MODEL 1u
+typedef struct {
+    bmm_opts best;     /* path and strassen_depth chosen; other fields default */
+    double est_ms;     /* its measured (or modelled) time per product */
+    int32_t measured;  /* 1: whole products timed; 0: leaf proxies + pass model */
+    int32_t candidates;
+} bmm_tune_result;
+bmm_status bmm_autotune(int32_t op, int64_t m, int64_t k, int64_t n, uint32_t flags,
+                        bmm_stream_t stream, bmm_tune_result *result);
+
+/* Forgets every recorded choice (all devices). */
+void bmm_autotune_clear(void);
+
 /* Batched independent products C_i = A_i B_i, i < count, of individual sizes
  * (each a multiple of 64), all in one persistent launch of the base case.
  * op[i]: 0 binary, 1 Boolean (cubic; the batch may mix them). The pointer

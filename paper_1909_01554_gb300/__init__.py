@@ -26,8 +26,11 @@ EXPORTED = [
     "bmm_gf2_batched", "bmm_bool_batched", "bmm_batched", "bmm_batched_plan_create",
     "bmm_batched_plan_run", "bmm_batched_plan_destroy", "bmm_transpose", "bmm_base_product",
     "bmm_basis_change", "bmm_stream_status", "bmm_status_string", "bmm_last_cuda_error",
-    "bmm_device_supported", "bmm_plan", "bmm_product_noalloc", "bmm_selftest_wait_timeout", "bmm_trace_enable", "bmm_trace_read", "bmm_launch_count",
+    "bmm_device_supported", "bmm_plan", "bmm_product_noalloc", "bmm_selftest_wait_timeout",
+    "bmm_trace_enable", "bmm_trace_read", "bmm_launch_count", "bmm_autotune",
+    "bmm_autotune_clear",
 ]
+TUNE_MODEL = 1
 PHASE_BASE, PHASE_XOR, PHASE_TRANSPOSE = 0, 1, 2
 
 
@@ -45,6 +48,11 @@ class Opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("strassen_depth", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("serial_depth", ctypes.c_int32),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("best", Opts), ("est_ms", ctypes.c_double), ("measured", ctypes.c_int32),
+                ("candidates", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -110,6 +118,11 @@ def _lib_handle():
         L.bmm_trace_read.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
         L.bmm_trace_read.restype = i32
         L.bmm_launch_count.restype = i64
+        L.bmm_autotune.argtypes = [i32, i64, i64, i64, ctypes.c_uint32, vp,
+                                   ctypes.POINTER(TuneResult)]
+        L.bmm_autotune.restype = i32
+        L.bmm_autotune_clear.argtypes = []
+        L.bmm_autotune_clear.restype = None
         _LIB = L
     return _LIB
 
@@ -203,6 +216,21 @@ def workspace_size(op: int, m: int, k: int, n: int, **kw) -> int:
     _check(_lib_handle().bmm_workspace_size(op, m, k, n, ctypes.byref(o), ctypes.byref(out)),
            "bmm_workspace_size")
     return int(out.value)
+
+
+def autotune(op: int, m: int, k: int, n: int, model: bool = False, stream=None) -> dict:
+    """Time the candidate (path, Strassen depth) pairs for this shape, record the
+    fastest for the planner's automatic choice and return it."""
+    r = TuneResult()
+    _check(_lib_handle().bmm_autotune(op, m, k, n, TUNE_MODEL if model else 0, _stream(stream),
+                                      ctypes.byref(r)), "bmm_autotune")
+    return {"path": r.best.path, "strassen_depth": r.best.strassen_depth, "est_ms": r.est_ms,
+            "measured": bool(r.measured), "candidates": r.candidates}
+
+
+def autotune_clear() -> None:
+    """Forget every recorded tuning choice."""
+    _lib_handle().bmm_autotune_clear()
 
 
 def plan(op: int, m: int, k: int, n: int, **kw) -> dict:

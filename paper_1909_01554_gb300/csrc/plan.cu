@@ -171,6 +171,16 @@ bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* op
             d++;
         p.depth = d;
     }
+    // A tuned choice (bmm_autotune) replaces the rules below when both the
+    // path and the depth are left to the library.
+    int tpath = 0, tdepth = 0;
+    const bool tuned = o.path == BMM_PATH_AUTO && o.strassen_depth < 0 &&
+                       tuned_choice(op, m, k, n, &tpath, &tdepth) &&
+                       (tdepth == 0 || (op == OP_GF2 && divisible(m, k, n, tdepth)));
+    if (tuned) {
+        p.depth = tdepth;
+        o.path = tpath;
+    }
     // base-case path: the tensor cores whenever the leaves allow TMA tiles
     // (k of a leaf a multiple of 128 bits), as SM pairs where clusters can be
     // launched (faster at every measured size from 4096^3 up), else the
@@ -201,6 +211,48 @@ bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* op
     p.workspace_bytes = workspace_for(m, k, n, p.depth, p.serial);
     *out = p;
     return BMM_OK;
+}
+
+uint64_t plan_pass_bytes(const Plan& p) {
+    uint32_t xi[7], eta[7], zeta[4];
+    switch (p.variant) {
+        case 0: slp::level_masks<0>(xi, eta, zeta); break;
+        case 1: slp::level_masks<1>(xi, eta, zeta); break;
+        default: slp::level_masks<2>(xi, eta, zeta); break;
+    }
+    auto bits = [](uint32_t x) { return (uint64_t)__builtin_popcount(x); };
+    uint64_t total = 2 * ((uint64_t)p.k * p.n / 8);  // transpose
+    uint64_t reps = 1;                              // executions of the current level
+    for (int l = 0; l < p.serial; l++, reps *= 7) {
+        const uint64_t a = (uint64_t)(p.m >> (l + 1)) * (p.k >> (l + 1)) / 8;
+        const uint64_t b = (uint64_t)(p.n >> (l + 1)) * (p.k >> (l + 1)) / 8;
+        const uint64_t c = (uint64_t)(p.m >> (l + 1)) * (p.n >> (l + 1)) / 8;
+        uint64_t per = 0;
+        uint32_t first = 0xF;
+        for (int h = 0; h < 7; h++) {
+            per += (bits(xi[h]) + 1) * a + (bits(eta[h]) + 1) * b;
+            uint32_t dest = 0;
+            for (int q = 0; q < 4; q++) dest |= ((zeta[q] >> h) & 1u) << q;
+            if (dest) {
+                per += c + bits(dest) * c + bits(dest & ~first) * c;  // R, C writes, C reads
+                first &= ~dest;
+            }
+        }
+        total += reps * per;
+    }
+    const int dp = p.depth - p.serial;
+    if (dp > 0) {
+        const uint64_t r = (uint64_t)ipow7(dp);
+        const int s = p.serial, d = p.depth;
+        const uint64_t in_a = (uint64_t)(p.m >> s) * (p.k >> s) / 8;
+        const uint64_t in_b = (uint64_t)(p.n >> s) * (p.k >> s) / 8;
+        const uint64_t out_c = (uint64_t)(p.m >> s) * (p.n >> s) / 8;
+        const uint64_t la = (uint64_t)(p.m >> d) * (p.k >> d) / 8;
+        const uint64_t lb = (uint64_t)(p.n >> d) * (p.k >> d) / 8;
+        const uint64_t lc = (uint64_t)(p.m >> d) * (p.n >> d) / 8;
+        total += reps * (in_a + r * la + in_b + r * lb + r * lc + out_c);
+    }
+    return total;
 }
 
 bmm_status execute_plan(const Plan& p, const uint64_t* A, const uint64_t* B, uint64_t* C,

@@ -19,6 +19,16 @@ struct Plan {
 };
 
 bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* opts, Plan* out);
+
+// Bytes the plan's streaming passes move through HBM: the transpose of B and
+// every XOR pass (depth-first combine / fold, breadth-first expand /
+// compress), not counting the base case.
+uint64_t plan_pass_bytes(const Plan& p);
+
+// The autotuner's recorded choice for (op, m, k, n) on the current device:
+// base-case path and Strassen depth. False if the shape was not tuned.
+bool tuned_choice(int op, int64_t m, int64_t k, int64_t n, int* path, int* depth);
+
 bmm_status execute_plan(const Plan& p, const uint64_t* A, const uint64_t* B, uint64_t* C,
                         void* workspace, cudaStream_t s);
 

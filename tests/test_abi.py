@@ -68,3 +68,19 @@ def test_argument_checks_need_no_gpu(built_lib):
     assert L.bmm_transpose(0, 16, 64, 64, None) == bmm.ERR_INVALID
     assert L.bmm_basis_change(1, 0, 16, 96, 128, 1, None) == bmm.ERR_INVALID
     assert L.bmm_basis_change(7, 0, 16, 128, 128, 1, None) == bmm.ERR_INVALID
+
+
+def test_autotune_argument_checks_need_no_gpu(built_lib):
+    """The autotuner rejects bad operations, sizes and flags before any CUDA call."""
+    import ctypes
+
+    import paper_1909_01554_gb300 as bmm
+
+    L = bmm.lib()
+    r = bmm.TuneResult()
+    assert L.bmm_autotune(2, 64, 64, 64, 0, None, ctypes.byref(r)) == bmm.ERR_INVALID
+    assert L.bmm_autotune(0, 96, 64, 64, 0, None, ctypes.byref(r)) == bmm.ERR_INVALID
+    assert L.bmm_autotune(1, 64, 0, 64, 0, None, ctypes.byref(r)) == bmm.ERR_INVALID
+    assert L.bmm_autotune(0, 64, 64, 64, 4, None, ctypes.byref(r)) == bmm.ERR_INVALID
+    assert L.bmm_autotune(0, 64, 64, 64, 0, None, None) == bmm.ERR_INVALID
+    L.bmm_autotune_clear()

@@ -303,8 +303,10 @@ def main():
             tuned["gf2"] = bmm.autotune(bmm.GF2, m, k, n, stream=sh)
         tuned["bool"] = bmm.autotune(bmm.BOOL, m, k, n, stream=sh)
 
-    def step(A1, B1, C1, A2, B2, C2):
+    def step(A1, B1, C1, A2, B2, C2, mid=None):
         bmm.gf2(A1, B1, C1, m, k, n, stream=sh, **kw_g)
+        if mid is not None:
+            mid.record(stream)
         bmm.boolean(A2, B2, C2, m, k, n, stream=sh, **kw_b)
 
     for _ in range(args.warmup):
@@ -321,13 +323,23 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     barrier()
+    # step boundaries and the point between the two products of each step
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
     ev0.record(stream)
-    for _ in range(args.steps):
-        step(Ag, Bg, Cg, Ab, Bb, Cb)
+    marks[0].record(stream)
+    for i in range(args.steps):
+        step(Ag, Bg, Cg, Ab, Bb, Cb, mid=marks[2 * i + 1])
+        marks[2 * i + 2].record(stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
+    per_product = {
+        "gf2": sum(marks[2 * i].elapsed_time(marks[2 * i + 1]) for i in range(args.steps))
+        / args.steps,
+        "bool": sum(marks[2 * i + 1].elapsed_time(marks[2 * i + 2]) for i in range(args.steps))
+        / args.steps,
+    }
     launches = bmm.launch_count() - l0
     bmm.trace_enable(False)
     bmm.stream_status(sh)
@@ -423,6 +435,8 @@ def main():
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
+            "product_ms": per_product,
+            "product_bops": {op: 2 * m * k * n / (t / 1000.0) for op, t in per_product.items()},
             "phases_ms_per_step": {"base": base_ms / args.steps, "xor": xor_ms / args.steps,
                                    "transpose": tr_ms / args.steps},
             "phase_launches": {"base": base_n, "xor": xor_n, "transpose": tr_n},

@@ -52,6 +52,35 @@ FP8_PER_BF16 = 2.0
 # with back-to-back MMAs); 2 FLOP each.
 FP8_MAC_PER_SM_CLK = 8192
 
+# DRAM bytes (read + write) of the base-case launches of one step of the
+# default workload, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum; profiles/tc_nt_kernel_square32768_traffic.md). It
+# holds only for the kernel source it was taken on and the same launches
+# (GF(2) depth 3 with one depth-first level: 7 leaf launches + 1 Boolean).
+TRAFFIC_RECORD = {
+    "kernel": "paper_1909_01554_gb300/csrc/tc_gemm.cu",
+    "sha256": "727c788512da4302461f087c926e1a0a943f3900a54f22964da11ebe3b03a038",
+    "workload": "square32768", "gf2_depth": 3, "gf2_serial": 1, "base_launches": 8,
+    "dram_bytes_per_step": 2787886592,
+}
+
+
+def recorded_traffic(workload: str, depth: int, serial: int, launches_per_step: float):
+    """Bytes per base-case launch from the ncu record, or None when the kernel
+    source or the launch composition differs from what was captured."""
+    import hashlib
+
+    r = TRAFFIC_RECORD
+    try:
+        with open(os.path.join(ROOT, r["kernel"]), "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    if (digest != r["sha256"] or workload != r["workload"] or depth != r["gf2_depth"]
+            or serial != r["gf2_serial"] or launches_per_step != r["base_launches"]):
+        return None
+    return r["dram_bytes_per_step"] / r["base_launches"]
+
 
 def tensor_pipe(achieved: float, clocks: dict, fallback_mhz: float) -> dict:
     """The tensor pipe's own limit at the clock seen under load, beside the
@@ -363,8 +392,12 @@ def main():
     if resolved in (bmm.PATH_TC_FP8, bmm.PATH_TC_FP8_PAIR, bmm.PATH_TC_I8):
         peak = pk["bf16_tflops_sustained"] * FP8_PER_BF16
         achieved = flops_base_step * args.steps / (base_ms / 1000.0) / 1e12
+        traffic = recorded_traffic(args.workload, depth_g, pg["serial_depth"],
+                                   base_n / args.steps)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_algorithmic": (7 ** depth_g * (lm * lk + ln * lk + lm * ln)
+                                        + m * k + k * n + m * n) / 8 / (base_n / args.steps),
                 "peak_source": f"{pk_kind} bf16 sustained x {FP8_PER_BF16} (nominal fp8:bf16)",
                 **tensor_pipe(achieved, clocks, pk["sm_max_mhz"])}
         dtype = "u8" if resolved == bmm.PATH_TC_I8 else "e4m3"

@@ -83,7 +83,11 @@ constexpr int AEXP_WARPS = 4;
 constexpr int TMA_WARP = 16;
 constexpr int MMA_WARP = 17;
 constexpr int THREADS = 18 * 32;
-constexpr int GROUP_M = 16;      // tile raster: 16 row-tiles per group
+// Tile raster: groups of GROUP_M row-tiles, column by column within a
+// group. Each Bt tile is read from DRAM once per group while the group's
+// rows of A (32 x 256 rows x k bits: 32 MiB at k = 32768 for pairs) stay in
+// L2 (measured: 64 row-tiles no longer fit and A is re-read).
+constexpr int GROUP_M = 32;
 
 constexpr int ACC_COL = 0;               // accumulator: TMEM columns [0, BN)
 constexpr int A_COL = BN;                // A ring: columns [BN, BN + ESTAGES * KS / 4)

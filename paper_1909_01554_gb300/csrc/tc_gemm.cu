@@ -846,24 +846,43 @@ bool make_map(CUtensorMap* map, const uint64_t* base, int64_t kwords, int64_t ro
     return r == CUDA_SUCCESS;
 }
 
-template <bool BATCHED, bool PAIR>
-cudaError_t set_smem_attr() {
-    static std::once_flag once;
-    static cudaError_t err = cudaSuccess;
-    std::call_once(once, [] {
-        err = cudaFuncSetAttribute(tc_nt_kernel<BATCHED, PAIR>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   Lay<PAIR>::SMEM_BYTES);
-    });
-    return err;
+constexpr int MAX_DEVICES = 64;
+
+int current_device() {
+    int d = 0;
+    cudaGetDevice(&d);
+    return d;
 }
 
-// CTA pairs that can be resident at once (clusters of two on one TPC).
+// Per-device one-time setup (function attributes and occupancy are per device).
+std::mutex g_setup_mu;
+
+template <bool BATCHED, bool PAIR>
+cudaError_t set_smem_attr() {
+    static bool done[MAX_DEVICES] = {false};
+    static cudaError_t err[MAX_DEVICES];
+    const int d = current_device();
+    if (d < 0 || d >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!done[d]) {
+        err[d] = cudaFuncSetAttribute(tc_nt_kernel<BATCHED, PAIR>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      Lay<PAIR>::SMEM_BYTES);
+        done[d] = true;
+    }
+    return err[d];
+}
+
+// CTA pairs that can be resident at once on the current device (clusters of
+// two on one TPC); 0 if cluster launches are unavailable.
 int pair_slots() {
-    static std::once_flag once;
-    static int slots = 0;
-    std::call_once(once, [] {
-        if (set_smem_attr<false, true>() != cudaSuccess) return;
+    static int slots[MAX_DEVICES];
+    static bool done[MAX_DEVICES] = {false};
+    const int d = current_device();
+    if (d < 0 || d >= MAX_DEVICES) return 0;
+    if (set_smem_attr<false, true>() != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!done[d]) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(2 * (unsigned)sm_count());
         cfg.blockDim = dim3(THREADS);
@@ -876,12 +895,14 @@ int pair_slots() {
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, tc_nt_kernel<false, true>, &cfg) == cudaSuccess)
-            slots = n;
-        else
+        if (cudaOccupancyMaxActiveClusters(&n, tc_nt_kernel<false, true>, &cfg) != cudaSuccess) {
             (void)cudaGetLastError();
-    });
-    return slots;
+            n = 0;
+        }
+        slots[d] = n;
+        done[d] = true;
+    }
+    return slots[d];
 }
 
 // units: CTAs (single) or CTA pairs (PAIR) to launch.

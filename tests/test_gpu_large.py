@@ -74,16 +74,27 @@ def run_product(op, n, seed, ids, p, **kw):
 
 
 def test_config2_square32768_bench_launch_configuration():
-    """m = k = n = 32768, seed 2: GF(2) p = 1/2 through the planner's default
-    (2-level self-inverse Strassen on the tensor base case), Boolean p = 2^-7.5
-    cubic - exactly the calls bench.py times."""
+    """m = k = n = 32768, seed 2: GF(2) p = 1/2 and Boolean p = 2^-7.5 in the
+    configuration bench.py times (autotuned first, as the bench does: for
+    GF(2) a self-inverse Strassen depth on the tensor base case), and GF(2)
+    also at the planner's untuned rule (depth 2)."""
     n, seed = 32768, 2
-    info = bmm.plan(bmm.GF2, n, n, n)
-    assert info["strassen_depth"] == 2 and info["leaves"] == 49
+    bmm.autotune_clear()
+    assert bmm.plan(bmm.GF2, n, n, n)["strassen_depth"] == 2  # the untuned rule
     Cg = run_product(bmm.GF2, n, seed, IDS_GF2, None)
     sampled_check(bmm.GF2, n, seed, IDS_GF2, None, Cg)
+    del Cg
+    tg = bmm.autotune(bmm.GF2, n, n, n)
+    tb = bmm.autotune(bmm.BOOL, n, n, n)
+    info = bmm.plan(bmm.GF2, n, n, n)
+    assert (info["path"], info["strassen_depth"]) == (tg["path"], tg["strassen_depth"])
+    Cg = run_product(bmm.GF2, n, seed, IDS_GF2, None)
+    sampled_check(bmm.GF2, n, seed, IDS_GF2, None, Cg)
+    del Cg
+    assert bmm.plan(bmm.BOOL, n, n, n)["path"] == tb["path"]
     Cb = run_product(bmm.BOOL, n, seed, IDS_BOOL, "2^-7.5")
     sampled_check(bmm.BOOL, n, seed, IDS_BOOL, "2^-7.5", Cb)
+    bmm.autotune_clear()
 
 
 def test_config3_square65536_paths_agree():
@@ -103,7 +114,13 @@ def test_config3_square65536_paths_agree():
         del tp
         if op == bmm.GF2:
             st = run_product(op, n, seed, ids, p)
-            assert (st == tc).all(), "Strassen vs cubic disagree"
+            assert (st == tc).all(), "Strassen (planner rule) vs cubic disagree"
+            del st
+            bmm.autotune(op, n, n, n)  # the configuration bench.py times
+            st = run_product(op, n, seed, ids, p)
+            bmm.autotune_clear()
+            assert (st == tc).all(), "Strassen (autotuned) vs cubic disagree"
+            del st
         sampled_check(op, n, seed, ids, p, tc, nrows=4, ncols=4, freivalds=4)
 
 

@@ -13,9 +13,11 @@
 namespace bmm {
 
 cudaError_t launch_expand(int variant, int operand, int d, const uint64_t* X, int64_t pitch,
-                          int64_t rows, int64_t wcols, uint64_t* leaves, cudaStream_t s);
+                          int64_t rows, int64_t wcols, uint32_t mask, uint64_t* leaves,
+                          cudaStream_t s);
 cudaError_t launch_compress(int variant, int d, const uint64_t* leaves, int64_t lr, int64_t lw,
-                            uint64_t* C, int64_t ldc, cudaStream_t s);
+                            uint64_t* C, int64_t ldc, uint32_t dest, uint32_t first,
+                            cudaStream_t s);
 cudaError_t launch_combine(int operand, const uint64_t* X, int64_t pitch, int64_t hr, int64_t hw,
                            uint32_t mask, uint64_t* dst, cudaStream_t s);
 cudaError_t launch_fold(const uint64_t* R, int64_t hr, int64_t hw, uint64_t* C, int64_t ldc,
@@ -45,11 +47,18 @@ bool divisible(int64_t m, int64_t k, int64_t n, int d) {
     return (m % ((int64_t)1 << d) == 0) && (m >> d) % 64 == 0 && k % unit == 0 && n % unit == 0;
 }
 
+// The last depth-first level hands its branches straight to the
+// breadth-first passes: its input combination is done by the expanding pass
+// (reading the parent's quadrants) and its output fold by the compressing
+// pass, so that level needs no branch buffers.
+bool fused_last_serial(int depth, int serial) { return serial > 0 && depth > serial; }
+
 // Bytes of scratch for a plan: Bt, the depth-first branch buffers of every
 // serial level, and the breadth-first leaves at the bottom.
 uint64_t workspace_for(int64_t m, int64_t k, int64_t n, int depth, int serial) {
     uint64_t b = round_up((uint64_t)k * n / 8);  // Bt
-    for (int l = 1; l <= serial; l++) {
+    const int bufs = fused_last_serial(depth, serial) ? serial - 1 : serial;
+    for (int l = 1; l <= bufs; l++) {
         b += round_up((uint64_t)(m >> l) * (k >> l) / 8);
         b += round_up((uint64_t)(n >> l) * (k >> l) / 8);
         b += round_up((uint64_t)(m >> l) * (n >> l) / 8);
@@ -88,7 +97,8 @@ struct Exec {
             return q;
         };
         Bt = take((uint64_t)p.k * p.n / 8);
-        for (int l = 1; l <= p.serial; l++) {
+        const int bufs = fused_last_serial(p.depth, p.serial) ? p.serial - 1 : p.serial;
+        for (int l = 1; l <= bufs; l++) {
             T[l] = take((uint64_t)(p.m >> l) * (p.k >> l) / 8);
             S[l] = take((uint64_t)(p.n >> l) * (p.k >> l) / 8);
             R[l] = take((uint64_t)(p.m >> l) * (p.n >> l) / 8);
@@ -107,6 +117,18 @@ struct Exec {
         if (l < p.serial) {
             const int64_t hm = m / 2, hk = k / 2, hn = n / 2;
             uint32_t first = 0xF;
+            if (l + 1 == p.serial && fused_last_serial(p.depth, p.serial)) {
+                for (int h = 0; h < 7; h++) {
+                    uint32_t dest = 0;
+                    for (int q = 0; q < 4; q++) dest |= ((zeta[q] >> h) & 1u) << q;
+                    if (!dest) continue;
+                    bmm_status st = leaves(A, lda, xi[h], B, ldb, eta[h], C, ldc, dest,
+                                           first & dest, hm, hk, hn);
+                    if (st != BMM_OK) return st;
+                    first &= ~dest;
+                }
+                return BMM_OK;
+            }
             for (int h = 0; h < 7; h++) {
                 BMM_CUDA_TRY(launch_combine(0, A, lda, hm, hk / 64, xi[h], T[l + 1], s));
                 BMM_CUDA_TRY(launch_combine(1, B, ldb, hn, hk / 64, eta[h], S[l + 1], s));
@@ -122,18 +144,29 @@ struct Exec {
             }
             return BMM_OK;
         }
-        const int dp = p.depth - l;
-        if (dp == 0)
+        if (p.depth == l)
             return run_base_product(p.op, p.path, A, lda, B, ldb, C, ldc, m, k, n, s);
+        return leaves(A, lda, 0, B, ldb, 0, C, ldc, 0, 0, m, k, n);
+    }
+
+    // The breadth-first levels below an m x k x n block: expand both operands
+    // into the leaves, the batched base case, compress into C. With non-zero
+    // masks the block's operands are combinations of the quadrants of A / B
+    // (their parents) and the result is folded into the quadrants `dest` of
+    // C (its parent), as a depth-first level would.
+    bmm_status leaves(const uint64_t* A, int64_t lda, uint32_t amask, const uint64_t* B,
+                      int64_t ldb, uint32_t bmask, uint64_t* C, int64_t ldc, uint32_t dest,
+                      uint32_t first, int64_t m, int64_t k, int64_t n) {
+        const int dp = p.depth - p.serial;
         const int64_t lm = m >> dp, lk = k >> dp, ln = n >> dp;
-        BMM_CUDA_TRY(launch_expand(p.variant, 0, dp, A, lda, m, k / 64, TL, s));
-        BMM_CUDA_TRY(launch_expand(p.variant, 1, dp, B, ldb, n, k / 64, SL, s));
-        const int64_t leaves = ipow7(dp);
+        BMM_CUDA_TRY(launch_expand(p.variant, 0, dp, A, lda, m, k / 64, amask, TL, s));
+        BMM_CUDA_TRY(launch_expand(p.variant, 1, dp, B, ldb, n, k / 64, bmask, SL, s));
+        const int64_t count = ipow7(dp);
         bmm_status st = run_base_product_batched(p.op, p.path, TL, lk / 64, lm * lk / 64, SL,
                                                  lk / 64, ln * lk / 64, QL, ln / 64, lm * ln / 64,
-                                                 leaves, lm, lk, ln, s);
+                                                 count, lm, lk, ln, s);
         if (st != BMM_OK) return st;
-        BMM_CUDA_TRY(launch_compress(p.variant, dp, QL, lm, ln / 64, C, ldc, s));
+        BMM_CUDA_TRY(launch_compress(p.variant, dp, QL, lm, ln / 64, C, ldc, dest, first, s));
         return BMM_OK;
     }
 };
@@ -221,35 +254,41 @@ uint64_t plan_pass_bytes(const Plan& p) {
         default: slp::level_masks<2>(xi, eta, zeta); break;
     }
     auto bits = [](uint32_t x) { return (uint64_t)__builtin_popcount(x); };
+    const int dp = p.depth - p.serial, d = p.depth;
+    const bool fused = fused_last_serial(p.depth, p.serial);
+    const uint64_t r = (uint64_t)ipow7(dp > 0 ? dp : 0);
+    const uint64_t la = (uint64_t)(p.m >> d) * (p.k >> d) / 8;
+    const uint64_t lb = (uint64_t)(p.n >> d) * (p.k >> d) / 8;
+    const uint64_t lc = (uint64_t)(p.m >> d) * (p.n >> d) / 8;
     uint64_t total = 2 * ((uint64_t)p.k * p.n / 8);  // transpose
     uint64_t reps = 1;                              // executions of the current level
     for (int l = 0; l < p.serial; l++, reps *= 7) {
         const uint64_t a = (uint64_t)(p.m >> (l + 1)) * (p.k >> (l + 1)) / 8;
         const uint64_t b = (uint64_t)(p.n >> (l + 1)) * (p.k >> (l + 1)) / 8;
         const uint64_t c = (uint64_t)(p.m >> (l + 1)) * (p.n >> (l + 1)) / 8;
+        const bool last_fused = fused && l + 1 == p.serial;
         uint64_t per = 0;
         uint32_t first = 0xF;
         for (int h = 0; h < 7; h++) {
-            per += (bits(xi[h]) + 1) * a + (bits(eta[h]) + 1) * b;
             uint32_t dest = 0;
             for (int q = 0; q < 4; q++) dest |= ((zeta[q] >> h) & 1u) << q;
-            if (dest) {
-                per += c + bits(dest) * c + bits(dest & ~first) * c;  // R, C writes, C reads
-                first &= ~dest;
+            if (last_fused) {  // expand reads the parent's quadrants, compress folds
+                if (!dest) continue;
+                per += bits(xi[h]) * a + r * la + bits(eta[h]) * b + r * lb;
+                per += r * lc + bits(dest) * c + bits(dest & ~first) * c;
+            } else {  // combine into branch buffers, fold the branch result
+                per += (bits(xi[h]) + 1) * a + (bits(eta[h]) + 1) * b;
+                if (dest) per += c + bits(dest) * c + bits(dest & ~first) * c;
             }
+            first &= ~dest;
         }
         total += reps * per;
     }
-    const int dp = p.depth - p.serial;
-    if (dp > 0) {
-        const uint64_t r = (uint64_t)ipow7(dp);
-        const int s = p.serial, d = p.depth;
+    if (dp > 0 && !fused) {
+        const int s = p.serial;
         const uint64_t in_a = (uint64_t)(p.m >> s) * (p.k >> s) / 8;
         const uint64_t in_b = (uint64_t)(p.n >> s) * (p.k >> s) / 8;
         const uint64_t out_c = (uint64_t)(p.m >> s) * (p.n >> s) / 8;
-        const uint64_t la = (uint64_t)(p.m >> d) * (p.k >> d) / 8;
-        const uint64_t lb = (uint64_t)(p.n >> d) * (p.k >> d) / 8;
-        const uint64_t lc = (uint64_t)(p.m >> d) * (p.n >> d) / 8;
         total += reps * (in_a + r * la + in_b + r * lb + r * lc + out_c);
     }
     return total;

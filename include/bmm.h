@@ -59,7 +59,8 @@ typedef enum {
 typedef enum {
     BMM_PATH_AUTO = 0,    /* the fastest path for the shape on this device */
     BMM_PATH_TC_FP8 = 1,  /* tcgen05 tensor cores, bits -> e4m3, FP32 accumulate */
-    BMM_PATH_TC_I8 = 2,   /* tcgen05 tensor cores, bits -> u8, S32 accumulate */
+    BMM_PATH_TC_I8 = 2,   /* 8-bit integer tensor MMA: sm_103a has none, so requests
+                             for it return BMM_ERR_UNSUPPORTED */
     BMM_PATH_POPC = 3,    /* CUDA cores: LOP3 AND-XOR / AND-OR over 32-bit words */
     BMM_PATH_TC_FP8_PAIR = 4 /* as TC_FP8, two SMs per 256 x 256 tile (cta_group::2) */
 } bmm_path;
@@ -187,7 +188,9 @@ bmm_status bmm_transpose(const uint64_t *X, uint64_t *Xt, int64_t rows, int64_t 
 
 /* Base-case product in the "NT" form: C (m x n) = A (m x k) times the
  * transpose of Bt (n x k), over GF(2) (op 0) or Boolean (op 1), on one path
- * (Sec. 3.10; Sec. 3.18). */
+ * (Sec. 3.10; Sec. 3.18). `path` must be explicit (not BMM_PATH_AUTO); the
+ * tensor-core paths need k % 128 == 0 and an sm_103 device, else
+ * BMM_ERR_UNSUPPORTED. */
 bmm_status bmm_base_product(int32_t op, int32_t path, const uint64_t *A, const uint64_t *Bt,
                             uint64_t *C, int64_t m, int64_t k, int64_t n, bmm_stream_t stream);
 

@@ -341,18 +341,26 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t tmem) {
                      : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+// 32 lanes x 64 columns (one row per thread), then wait for the load.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-        "[%32];"
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
+        "%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
+        "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, "
+        "[%64];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
           "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
           "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
           "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-          "=r"(v[31])
+          "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]),
+          "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]),
+          "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]),
+          "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]),
+          "=r"(v[55]), "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]),
+          "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -407,7 +415,7 @@ __device__ __forceinline__ void spread8(uint32_t x, const Spread& sp, uint32_t* 
 // GF(2): v[j] = count * 2^-12 exactly; adding 2^11 puts count's LSB in bit 0.
 // Boolean: any non-zero count. Packed with a 5-level tree of multiply-adds.
 template <int OP>
-__device__ __forceinline__ uint32_t pack_bits(const uint32_t (&v)[32]) {
+__device__ __forceinline__ uint32_t pack_bits(const uint32_t* v) {
     uint32_t b[32];
 #pragma unroll
     for (int j = 0; j < 32; j++) {
@@ -774,14 +782,18 @@ __global__ void __launch_bounds__(THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-#pragma unroll 2
-                for (int c = 0; c < CW; c++) {
-                    uint32_t v[32];
-                    tmem_ld32(tmem + tlane + (uint32_t)(ACC_COL + 32 * (CW * chalf + c)), v);
-                    if (gf2)
+                // 64 columns per load: half the load-wait round trips of 32
+#pragma unroll
+                for (int c = 0; c < CW; c += 2) {
+                    uint32_t v[64];
+                    tmem_ld64(tmem + tlane + (uint32_t)(ACC_COL + 32 * (CW * chalf + c)), v);
+                    if (gf2) {
                         words[c] ^= pack_bits<OP_GF2>(v);
-                    else
+                        words[c + 1] ^= pack_bits<OP_GF2>(v + 32);
+                    } else {
                         words[c] |= pack_bits<OP_BOOL>(v);
+                        words[c + 1] |= pack_bits<OP_BOOL>(v + 32);
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();

@@ -54,10 +54,13 @@ def sampled_check(op, n, seed, ids, p, C, nrows=8, ncols=8, freivalds=8):
                              endpoint=True)
             assert (O.matvec_gf2(C, x, n, n) ==
                     O.matvec_gf2(A, O.matvec_gf2(B, x, n, n), n, n)).all(), "Freivalds"
-    # Boolean output density: k p^2 = 1 in every Boolean workload -> 1 - 1/e
+    # Output density: k p^2 = 1 in every Boolean workload -> 1 - 1/e; a GF(2)
+    # product of uniform random bits is uniform -> 1/2
+    dens = np.unpackbits(C[:: max(1, n // 512)].view(np.uint8)).mean()
     if op == bmm.BOOL:
-        dens = np.unpackbits(C[:: max(1, n // 512)].view(np.uint8)).mean()
         assert abs(dens - (1 - np.exp(-1))) < 0.02
+    else:
+        assert abs(dens - 0.5) < 0.01
 
 
 def run_product(op, n, seed, ids, p, **kw):

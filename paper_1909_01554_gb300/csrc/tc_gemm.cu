@@ -974,6 +974,8 @@ bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int6
     if (k % KS || (lda & 1) || (ldb & 1) || (count > 1 && ((strideA & 1) || (strideB & 1))))
         return BMM_ERR_UNSUPPORTED;
     if (m <= 0 || n <= 0 || k <= 0 || count <= 0) return BMM_OK;
+    // tile and stage indices are 32-bit in the kernel
+    if (m > 0x7fffffffLL || n > 0x7fffffffLL || k / KS > 0x3fffffffLL) return BMM_ERR_UNSUPPORTED;
     const int slots = pair ? pair_slots() : sm_count();
     if (slots <= 0) return BMM_ERR_UNSUPPORTED;
     uint32_t* err = device_error_word();

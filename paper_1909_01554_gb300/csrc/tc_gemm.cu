@@ -413,22 +413,23 @@ __device__ __forceinline__ void spread8(uint32_t x, const Spread& sp, uint32_t* 
 
 // 32 result bits of one accumulator row slice -> one word, bit j from v[j].
 // GF(2): v[j] = count * 2^-12 exactly; adding 2^11 puts count's LSB in bit 0.
-// Boolean: any non-zero count. Packed with a 5-level tree of multiply-adds.
+// Boolean: any non-zero count. Each bit goes in with one funnel shift (the
+// word shifts right by one and takes the bit at the top), in four
+// independent chains of eight that are merged at the end.
 template <int OP>
 __device__ __forceinline__ uint32_t pack_bits(const uint32_t* v) {
-    uint32_t b[32];
+    uint32_t c[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-    for (int j = 0; j < 32; j++) {
-        if (OP == OP_GF2)
-            b[j] = __float_as_uint(__uint_as_float(v[j]) + 2048.0f) & 1u;
-        else
-            b[j] = min(v[j], 1u);  // fp32 counts are >= 0: non-zero bits <=> count > 0
-    }
+    for (int j = 0; j < 8; j++)
 #pragma unroll
-    for (int w = 1; w < 32; w *= 2)
-#pragma unroll
-        for (int j = 0; j < 32; j += 2 * w) b[j] = b[j + w] * (1u << w) + b[j];
-    return b[0];
+        for (int g = 0; g < 4; g++) {
+            const uint32_t x = v[8 * g + j];
+            const uint32_t bit = OP == OP_GF2 ? __float_as_uint(__uint_as_float(x) + 2048.0f)
+                                              : min(x, 1u);  // fp32 counts are >= 0
+            c[g] = __funnelshift_r(c[g], bit, 1);  // bit 0 of `bit` enters at bit 31
+        }
+    // chain g holds bits 8g..8g+7 in its top byte
+    return (c[0] >> 24) | (c[1] >> 16) | (c[2] >> 8) | c[3];
 }
 
 struct TileCoord {

@@ -59,9 +59,9 @@ FP8_MAC_PER_SM_CLK = 8192
 # (GF(2) depth 3 with one depth-first level: 7 leaf launches + 1 Boolean).
 TRAFFIC_RECORD = {
     "kernel": "paper_1909_01554_gb300/csrc/tc_gemm.cu",
-    "sha256": "5c09241bbc6ec05ffa93df2b30fac9cb1ed3f0112f5afa8542f0f3fb6010df3c",
+    "sha256": "f7c45ea7c1a8abe8b51303a3ca45819ebae2c10ca9ef3f1bb93bc918553616ac",
     "workload": "square32768", "gf2_depth": 3, "gf2_serial": 1, "base_launches": 8,
-    "dram_bytes_per_step": 2781822208,
+    "dram_bytes_per_step": 2782232832,
 }
 
 

@@ -144,7 +144,7 @@ int64_t pow7(int d) {
 // Leaf products of one candidate, timed on a proxy and scaled.
 bmm_status model_leaves(int op, const Cand& c, cudaStream_t s, double* ms) {
     const int d = c.depth;
-    const int64_t ml = c.plan.m >> d, kl = c.plan.k >> d, nl = c.plan.n >> d;
+    const int64_t ml = c.plan.m >> d, kl = c.plan.kp >> d, nl = c.plan.n >> d;
     const int64_t mp = std::min<int64_t>(ml, 16384), kp = std::min<int64_t>(kl, 16384),
                   np = std::min<int64_t>(nl, 16384);
     const uint64_t a = (uint64_t)mp * kp / 8, b = (uint64_t)np * kp / 8, cc = (uint64_t)mp * np / 8;
@@ -204,7 +204,6 @@ extern "C" bmm_status bmm_autotune(int32_t op, int64_t m, int64_t k, int64_t n, 
     for (int path : paths) {
         for (int d = 0; d <= (op == OP_GF2 ? 4 : 0); d++) {
             if (d > 0 && ((m >> d) < 256 || (k >> d) < 256 || (n >> d) < 256)) continue;
-            if (path != BMM_PATH_POPC && ((k >> d) % 128) != 0) continue;
             bmm_opts o;
             bmm_opts_default(&o);
             o.path = path;

@@ -79,6 +79,7 @@ struct Exec {
     cudaStream_t s;
     uint32_t xi[7], eta[7], zeta[4];
     uint64_t* Bt = nullptr;
+    uint64_t* Apad = nullptr;  // A with k padded to kp (only when kp != k)
     uint64_t* T[8] = {nullptr};
     uint64_t* S[8] = {nullptr};
     uint64_t* R[8] = {nullptr};
@@ -96,18 +97,19 @@ struct Exec {
             off += round_up(bytes);
             return q;
         };
-        Bt = take((uint64_t)p.k * p.n / 8);
+        Bt = take((uint64_t)p.kp * p.n / 8);
+        if (p.kp != p.k) Apad = take((uint64_t)p.m * p.kp / 8);
         const int bufs = fused_last_serial(p.depth, p.serial) ? p.serial - 1 : p.serial;
         for (int l = 1; l <= bufs; l++) {
-            T[l] = take((uint64_t)(p.m >> l) * (p.k >> l) / 8);
-            S[l] = take((uint64_t)(p.n >> l) * (p.k >> l) / 8);
+            T[l] = take((uint64_t)(p.m >> l) * (p.kp >> l) / 8);
+            S[l] = take((uint64_t)(p.n >> l) * (p.kp >> l) / 8);
             R[l] = take((uint64_t)(p.m >> l) * (p.n >> l) / 8);
         }
         const int dp = p.depth - p.serial;
         if (dp > 0) {
             const uint64_t r = (uint64_t)ipow7(dp);
-            TL = take(r * (uint64_t)(p.m >> p.depth) * (p.k >> p.depth) / 8);
-            SL = take(r * (uint64_t)(p.n >> p.depth) * (p.k >> p.depth) / 8);
+            TL = take(r * (uint64_t)(p.m >> p.depth) * (p.kp >> p.depth) / 8);
+            SL = take(r * (uint64_t)(p.n >> p.depth) * (p.kp >> p.depth) / 8);
             QL = take(r * (uint64_t)(p.m >> p.depth) * (p.n >> p.depth) / 8);
         }
     }
@@ -173,6 +175,11 @@ struct Exec {
 
 }  // namespace
 
+// Scratch of a plan with k padded to kp (the padded copy of A when kp != k).
+uint64_t workspace_padded(int64_t m, int64_t k, int64_t kp, int64_t n, int depth, int serial) {
+    return workspace_for(m, kp, n, depth, serial) + (kp != k ? round_up((uint64_t)m * kp / 8) : 0);
+}
+
 bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* opts, Plan* out) {
     bmm_opts o;
     bmm_opts_default(&o);
@@ -214,18 +221,23 @@ bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* op
         p.depth = tdepth;
         o.path = tpath;
     }
-    // base-case path: the tensor cores whenever the leaves allow TMA tiles
-    // (k of a leaf a multiple of 128 bits), as SM pairs where clusters can be
-    // launched (faster at every measured size from 4096^3 up), else the
-    // CUDA-core kernel.
+    // base-case path: the tensor cores wherever the device has them, as SM
+    // pairs where clusters can be launched (faster at every measured size
+    // from 4096^3 up), else the CUDA-core kernel. The tensor paths pad k
+    // (below) so that every leaf's k is a multiple of 128 bits.
     if (o.path == BMM_PATH_AUTO) {
-        if (tc_path_available() && ((k >> p.depth) % 128) == 0)
+        if (tc_path_available())
             p.path = tc_pair_available() ? BMM_PATH_TC_FP8_PAIR : BMM_PATH_TC_FP8;
         else
             p.path = BMM_PATH_POPC;
-    }
-    else
+    } else {
         p.path = o.path;
+    }
+    p.kp = k;
+    if (p.path == BMM_PATH_TC_FP8 || p.path == BMM_PATH_TC_FP8_PAIR) {
+        const int64_t unit = (int64_t)128 << p.depth;  // leaf k a multiple of 128 bits
+        p.kp = (k + unit - 1) / unit * unit;
+    }
     // depth-first levels: at least depth - MAX_MERGED; more while the
     // breadth-first scratch does not fit in free device memory.
     int serial_min = p.depth > MAX_MERGED ? p.depth - MAX_MERGED : 0;
@@ -237,11 +249,11 @@ bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* op
         size_t fr = 0, tot = 0;
         if (!(o.workspace) && cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
             while (p.serial < p.depth &&
-                   workspace_for(m, k, n, p.depth, p.serial) > (uint64_t)(fr * 0.9))
+                   workspace_padded(m, k, p.kp, n, p.depth, p.serial) > (uint64_t)(fr * 0.9))
                 p.serial++;
         }
     }
-    p.workspace_bytes = workspace_for(m, k, n, p.depth, p.serial);
+    p.workspace_bytes = workspace_padded(m, k, p.kp, n, p.depth, p.serial);
     *out = p;
     return BMM_OK;
 }
@@ -257,14 +269,15 @@ uint64_t plan_pass_bytes(const Plan& p) {
     const int dp = p.depth - p.serial, d = p.depth;
     const bool fused = fused_last_serial(p.depth, p.serial);
     const uint64_t r = (uint64_t)ipow7(dp > 0 ? dp : 0);
-    const uint64_t la = (uint64_t)(p.m >> d) * (p.k >> d) / 8;
-    const uint64_t lb = (uint64_t)(p.n >> d) * (p.k >> d) / 8;
+    const uint64_t la = (uint64_t)(p.m >> d) * (p.kp >> d) / 8;
+    const uint64_t lb = (uint64_t)(p.n >> d) * (p.kp >> d) / 8;
     const uint64_t lc = (uint64_t)(p.m >> d) * (p.n >> d) / 8;
     uint64_t total = 2 * ((uint64_t)p.k * p.n / 8);  // transpose
+    if (p.kp != p.k) total += (uint64_t)p.m * p.k / 8 + (uint64_t)p.m * p.kp / 8;  // padded A
     uint64_t reps = 1;                              // executions of the current level
     for (int l = 0; l < p.serial; l++, reps *= 7) {
-        const uint64_t a = (uint64_t)(p.m >> (l + 1)) * (p.k >> (l + 1)) / 8;
-        const uint64_t b = (uint64_t)(p.n >> (l + 1)) * (p.k >> (l + 1)) / 8;
+        const uint64_t a = (uint64_t)(p.m >> (l + 1)) * (p.kp >> (l + 1)) / 8;
+        const uint64_t b = (uint64_t)(p.n >> (l + 1)) * (p.kp >> (l + 1)) / 8;
         const uint64_t c = (uint64_t)(p.m >> (l + 1)) * (p.n >> (l + 1)) / 8;
         const bool last_fused = fused && l + 1 == p.serial;
         uint64_t per = 0;
@@ -286,8 +299,8 @@ uint64_t plan_pass_bytes(const Plan& p) {
     }
     if (dp > 0 && !fused) {
         const int s = p.serial;
-        const uint64_t in_a = (uint64_t)(p.m >> s) * (p.k >> s) / 8;
-        const uint64_t in_b = (uint64_t)(p.n >> s) * (p.k >> s) / 8;
+        const uint64_t in_a = (uint64_t)(p.m >> s) * (p.kp >> s) / 8;
+        const uint64_t in_b = (uint64_t)(p.n >> s) * (p.kp >> s) / 8;
         const uint64_t out_c = (uint64_t)(p.m >> s) * (p.n >> s) / 8;
         total += reps * (in_a + r * la + in_b + r * lb + r * lc + out_c);
     }
@@ -297,8 +310,18 @@ uint64_t plan_pass_bytes(const Plan& p) {
 bmm_status execute_plan(const Plan& p, const uint64_t* A, const uint64_t* B, uint64_t* C,
                         void* workspace, cudaStream_t s) {
     Exec ex(p, workspace, s);
-    BMM_CUDA_TRY(launch_transpose(B, ex.Bt, p.k, p.n, s));
-    return ex.level(0, A, p.k / 64, ex.Bt, p.k / 64, C, p.n / 64, p.m, p.k, p.n);
+    const uint64_t* Aop = A;
+    if (p.kp != p.k) {
+        // zero pad columns k..kp of A (a pitched copy) and of B^T
+        const size_t wb = (size_t)(p.k / 8), pb = (size_t)(p.kp / 8);
+        BMM_CUDA_TRY(cudaMemset2DAsync((char*)ex.Apad + wb, pb, 0, pb - wb, (size_t)p.m, s));
+        BMM_CUDA_TRY(cudaMemcpy2DAsync(ex.Apad, pb, A, wb, wb, (size_t)p.m,
+                                       cudaMemcpyDeviceToDevice, s));
+        BMM_CUDA_TRY(cudaMemset2DAsync((char*)ex.Bt + wb, pb, 0, pb - wb, (size_t)p.n, s));
+        Aop = ex.Apad;
+    }
+    BMM_CUDA_TRY(launch_transpose_pitched(B, p.n / 64, ex.Bt, p.kp / 64, p.k, p.n, s));
+    return ex.level(0, Aop, p.kp / 64, ex.Bt, p.kp / 64, C, p.n / 64, p.m, p.kp, p.n);
 }
 
 bmm_status run_base_product(int op, int path, const uint64_t* A, int64_t lda, const uint64_t* Bt,

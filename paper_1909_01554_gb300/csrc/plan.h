@@ -15,6 +15,10 @@ struct Plan {
     int depth = 0;             // total Strassen levels (0 = cubic)
     int serial = 0;            // of which depth-first (top) levels
     int64_t m = 0, k = 0, n = 0;
+    // k the kernels run with: the tensor-core paths need every leaf's k to be
+    // a multiple of 128 bits, so k is rounded up with zero columns of A and
+    // zero rows of B (the product is unchanged); kp == k otherwise.
+    int64_t kp = 0;
     uint64_t workspace_bytes = 0;
 };
 

@@ -147,11 +147,33 @@ def test_base_product_exact_counts_past_2pow23(path):
 def test_cubic_product(op, m, k, n):
     p = None if op == bmm.GF2 else "1/32"
     Ah, Bh = gen(m, k, 7, 0, p), gen(k, n, 7, 1, p)
-    for path in paths():
-        if path != bmm.PATH_POPC and k % 128:
-            continue
+    for path in paths():  # the product calls pad k for the tensor paths
         got = run(op, Ah, Bh, m, k, n, path=path, depth=0)
         check(got, O.cubic(OPS[op], Ah, Bh, m, k, n), f"cubic op={op} path={path}")
+
+
+@pytest.mark.parametrize("m,k,n,depth", [(512, 320, 448, 0), (256, 64, 192, 0),
+                                         (1024, 384, 768, 1), (1024, 768, 512, 2)])
+def test_tensor_paths_pad_k(m, k, n, depth):
+    """k that is not a multiple of 128 bits per leaf: the tensor paths run on
+    a copy of A and a B^T padded with zero columns, which leaves the product
+    unchanged."""
+    if not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    for op in (bmm.GF2, bmm.BOOL):
+        if op == bmm.BOOL and depth:
+            continue
+        p = None if op == bmm.GF2 else "1/16"
+        Ah, Bh = gen(m, k, 37, 0, p), gen(k, n, 37, 1, p)
+        want = O.cubic(OPS[op], Ah, Bh, m, k, n)
+        for path in (bmm.PATH_TC_FP8, bmm.PATH_TC_FP8_PAIR):
+            info = bmm.plan(op, m, k, n, path=path, depth=depth)
+            assert info["path"] == path
+            check(run(op, Ah, Bh, m, k, n, path=path, depth=depth), want,
+                  f"padded k op={op} path={path} depth={depth}")
+        if depth == 0:  # the automatic choice takes a tensor path too
+            assert bmm.plan(op, m, k, n)["path"] in (bmm.PATH_TC_FP8, bmm.PATH_TC_FP8_PAIR)
+            check(run(op, Ah, Bh, m, k, n), want, f"padded k auto op={op}")
 
 
 def test_identity_and_zero():

@@ -719,23 +719,26 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int nks = tile_nks<BATCHED, PAIR>(p, i);
                 int kin = 0;
                 for (int ks = 0; ks < nks; ks += SUB, pit++) {
-                    if (kin == 0) {
-                        if (!mbar_wait(acc_empty, (seg & 1) ^ 1, p.err)) {
-                            ok = false;
-                            break;
-                        }
-                    }
                     // Every producer fills the slots in order, so one wait on
-                    // the last of WAITG consecutive slots covers them all.
-                    if (pit % LY::WAITG == 0) {
+                    // the last of WAITG consecutive slots covers them all. At a
+                    // tile's first stage the operands are checked before the
+                    // (longer) wait for the epilogue to free the accumulator.
+                    const bool group = pit % LY::WAITG == 0;
+                    if (group) {
                         const int w = pit + LY::WAITG - 1 < total_pit ? pit + LY::WAITG - 1
                                                                       : total_pit - 1;
                         if (!mbar_wait(full_o(w % OSLOTS), (w / OSLOTS) & 1, p.err)) {
                             ok = false;
                             break;
                         }
-                        tc_fence_after();
                     }
+                    if (kin == 0) {
+                        if (!mbar_wait(acc_empty, (seg & 1) ^ 1, p.err)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    if (group || kin == 0) tc_fence_after();
                     const int q = pit % OSLOTS;
 #pragma unroll
                     for (int sub = 0; sub < SUB; sub++) {
@@ -788,6 +791,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int c = 0; c < CW; c += 2) {
                     uint32_t v[64];
                     tmem_ld64(tmem + tlane + (uint32_t)(ACC_COL + 32 * (CW * chalf + c)), v);
+                    if (c + 2 == CW) {
+                        // every column this warp drains is in registers: hand the
+                        // accumulator back before packing the last chunk
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) arrive_leader(acc_empty);
+                    }
                     if (gf2) {
                         words[c] ^= pack_bits<OP_GF2>(v);
                         words[c + 1] ^= pack_bits<OP_GF2>(v + 32);
@@ -796,9 +806,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                         words[c + 1] |= pack_bits<OP_BOOL>(v + 32);
                     }
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) arrive_leader(acc_empty);
             }
             if (!ok) break;
             const int64_t row =

@@ -690,6 +690,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(empty_p(s));
             if (!mbar_wait(empty_o(q), ((pit / OSLOTS) & 1) ^ 1, p.err)) break;
+            tc_fence_after();  // the slot's MMAs (seen complete) before our TMEM stores
             uint32_t y[64];
             spread8(xa.x, sp, y);
             spread8(xa.y, sp, y + 8);

@@ -59,9 +59,9 @@ FP8_MAC_PER_SM_CLK = 8192
 # (GF(2) depth 3 with one depth-first level: 7 leaf launches + 1 Boolean).
 TRAFFIC_RECORD = {
     "kernel": "paper_1909_01554_gb300/csrc/tc_gemm.cu",
-    "sha256": "f7c45ea7c1a8abe8b51303a3ca45819ebae2c10ca9ef3f1bb93bc918553616ac",
+    "sha256": "7a0832a3a419c81fe92e1311f1e87b455972dcdf9b09dc0b22a42cab5ea8deab",
     "workload": "square32768", "gf2_depth": 3, "gf2_serial": 1, "base_launches": 8,
-    "dram_bytes_per_step": 2782232832,
+    "dram_bytes_per_step": 2780954112,
 }
 
 

@@ -48,9 +48,13 @@ IDS_BOOL = (4, 5)
 LOP3_LANES_PER_SM_CLK = 64
 # Nominal dense FP8 : BF16 tensor throughput ratio (4.5 : 2.25 PFLOP/s).
 FP8_PER_BF16 = 2.0
+# Nominal dense FP4 : BF16 tensor throughput ratio (13.5 : 2.25 PFLOP/s).
+FP4_PER_BF16 = 6.0
 # FP8 MACs per clock per SM of tcgen05.mma kind::f8f6f4 on sm_103 (measured
 # with back-to-back MMAs); 2 FLOP each.
 FP8_MAC_PER_SM_CLK = 8192
+# FP4 (kind::mxf4) MACs per clock per SM: the nominal FP4 : FP8 ratio (3 : 1).
+FP4_MAC_PER_SM_CLK = 24576
 
 # DRAM bytes (read + write) of the base-case launches of one step of the
 # default workload, from one ncu capture (dram__bytes_read.sum +
@@ -82,17 +86,25 @@ def recorded_traffic(workload: str, depth: int, serial: int, launches_per_step: 
     return r["dram_bytes_per_step"] / r["base_launches"]
 
 
-def tensor_pipe(achieved: float, clocks: dict, fallback_mhz: float) -> dict:
+def tensor_pipe(achieved: float, clocks: dict, fallback_mhz: float, fp4: bool = False) -> dict:
     """The tensor pipe's own limit at the clock seen under load, beside the
     measured-peak roofline."""
     import torch
 
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     mhz = (clocks or {}).get("sm_mhz") or fallback_mhz
-    pp = sms * FP8_MAC_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
+    macs, kind = (FP4_MAC_PER_SM_CLK, "fp4") if fp4 else (FP8_MAC_PER_SM_CLK, "fp8")
+    pp = sms * macs * 2 * mhz * 1e6 / 1e12
     return {"pipe_peak": pp, "pipe_frac": achieved / pp,
-            "pipe_peak_source": f"{sms} SMs x {FP8_MAC_PER_SM_CLK} fp8 MAC/clk x 2 x "
+            "pipe_peak_source": f"{sms} SMs x {macs} {kind} MAC/clk x 2 x "
                                 f"{mhz} MHz (median under load)"}
+
+
+def tensor_peak(pk: dict, pk_kind: str, fp4: bool):
+    """Measured bf16 peak scaled to the operand type by the nominal ratio."""
+    ratio, kind = (FP4_PER_BF16, "fp4") if fp4 else (FP8_PER_BF16, "fp8")
+    return (pk["bf16_tflops_sustained"] * ratio,
+            f"{pk_kind} bf16 sustained x {ratio} (nominal {kind}:bf16)")
 
 
 def parse():
@@ -102,7 +114,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
-    ap.add_argument("--path", choices=["auto", "fp8", "fp8pair", "i8", "popc"], default="auto")
+    ap.add_argument("--path", choices=["auto", "fp8", "fp8pair", "fp4pair", "i8", "popc"],
+                    default="auto")
     ap.add_argument("--depth", type=int, default=-1, help="Strassen depth of the GF(2) product")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -341,7 +354,8 @@ def main():
     n, seed, bool_p = WORKLOADS[args.workload]
     m = k = n
     path = {"auto": bmm.PATH_AUTO, "fp8": bmm.PATH_TC_FP8, "i8": bmm.PATH_TC_I8,
-            "popc": bmm.PATH_POPC, "fp8pair": bmm.PATH_TC_FP8_PAIR}[args.path]
+            "popc": bmm.PATH_POPC, "fp8pair": bmm.PATH_TC_FP8_PAIR,
+            "fp4pair": bmm.PATH_TC_FP4_PAIR}[args.path]
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
 
@@ -421,8 +435,9 @@ def main():
     flops_base_step = 2 * leaves * lm * lk * ln + 2 * m * k * n  # GF(2) leaves + Boolean
     resolved = pg["path"]
     pk, pk_kind = peaks()
-    if resolved in (bmm.PATH_TC_FP8, bmm.PATH_TC_FP8_PAIR, bmm.PATH_TC_I8):
-        peak = pk["bf16_tflops_sustained"] * FP8_PER_BF16
+    if resolved in (*bmm.TENSOR_PATHS, bmm.PATH_TC_I8):
+        fp4 = resolved == bmm.PATH_TC_FP4_PAIR
+        peak, peak_source = tensor_peak(pk, pk_kind, fp4)
         achieved = flops_base_step * args.steps / (base_ms / 1000.0) / 1e12
         traffic = recorded_traffic(args.workload, depth_g, pg["serial_depth"],
                                    base_n / args.steps)
@@ -430,9 +445,9 @@ def main():
                 "frac": achieved / peak, "traffic": traffic,
                 "traffic_algorithmic": (7 ** depth_g * (lm * lk + ln * lk + lm * ln)
                                         + m * k + k * n + m * n) / 8 / (base_n / args.steps),
-                "peak_source": f"{pk_kind} bf16 sustained x {FP8_PER_BF16} (nominal fp8:bf16)",
-                **tensor_pipe(achieved, clocks, pk["sm_max_mhz"])}
-        dtype = "u8" if resolved == bmm.PATH_TC_I8 else "e4m3"
+                "peak_source": peak_source,
+                **tensor_pipe(achieved, clocks, pk["sm_max_mhz"], fp4)}
+        dtype = "u8" if resolved == bmm.PATH_TC_I8 else "e2m1" if fp4 else "e4m3"
     else:
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         peak = sms * LOP3_LANES_PER_SM_CLK * pk["sm_max_mhz"] * 1e6 * 64 / 1e12
@@ -638,12 +653,12 @@ def run_batched(args):
     bmm.trace_enable(False)
     base_n, base_ms = bmm.trace_read(bmm.PHASE_BASE)
     pk, pk_kind = peaks()
-    peak = pk["bf16_tflops_sustained"] * FP8_PER_BF16
+    fp4 = plan.path() == bmm.PATH_TC_FP4_PAIR
+    peak, peak_source = tensor_peak(pk, pk_kind, fp4)
     achieved = bops_step / (base_ms / 1000.0) / 1e12 if base_ms > 0 else 0.0
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
-            "peak_source": f"{pk_kind} bf16 sustained x {FP8_PER_BF16} (nominal fp8:bf16)",
-            **tensor_pipe(achieved, clocks, pk["sm_max_mhz"])}
+            "frac": achieved / peak, "traffic": None, "peak_source": peak_source,
+            **tensor_pipe(achieved, clocks, pk["sm_max_mhz"], fp4)}
 
     # the same products as one library call per problem
     def per_problem():
@@ -715,7 +730,8 @@ def run_batched(args):
         line = {
             "metric": METRIC, "value": value, "unit": "bop/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e4m3",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "e2m1" if fp4 else "e4m3",
             "data": "synthetic (seeded SplitMix64 Bernoulli bits)",
             "config": {"workload": args.workload, "problems": count,
                        "shapes": "m, k, n log-uniform in [256, 8192], multiples of 64",

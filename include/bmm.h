@@ -62,7 +62,10 @@ typedef enum {
     BMM_PATH_TC_I8 = 2,   /* 8-bit integer tensor MMA: sm_103a has none, so requests
                              for it return BMM_ERR_UNSUPPORTED */
     BMM_PATH_POPC = 3,    /* CUDA cores: LOP3 AND-XOR / AND-OR over 32-bit words */
-    BMM_PATH_TC_FP8_PAIR = 4 /* as TC_FP8, two SMs per 256 x 256 tile (cta_group::2) */
+    BMM_PATH_TC_FP8_PAIR = 4, /* as TC_FP8, two SMs per 256 x 256 tile (cta_group::2) */
+    BMM_PATH_TC_FP4_PAIR = 5  /* as TC_FP8_PAIR with bits -> e2m1 nibbles and the
+                                 block-scaled 4-bit MMA (kind::mxf4, unit-free scale
+                                 2^-6), FP32 accumulate: twice the k per MMA */
 } bmm_path;
 
 /* 2x2 recursion for the binary product. */
@@ -176,8 +179,16 @@ typedef struct bmm_batched_plan_s *bmm_batched_plan;
 bmm_status bmm_batched_plan_create(int32_t count, const int32_t *op, const uint64_t *const *A,
                                    const uint64_t *const *B, uint64_t *const *C, const int64_t *m,
                                    const int64_t *k, const int64_t *n, bmm_batched_plan *plan);
+/* As create, every problem on base-case `path` (bmm_path; AUTO as create;
+ * an explicit tensor path the device lacks: BMM_ERR_UNSUPPORTED). */
+bmm_status bmm_batched_plan_create_ex(int32_t count, const int32_t *op, const uint64_t *const *A,
+                                      const uint64_t *const *B, uint64_t *const *C,
+                                      const int64_t *m, const int64_t *k, const int64_t *n,
+                                      int32_t path, bmm_batched_plan *plan);
 bmm_status bmm_batched_plan_run(bmm_batched_plan plan, bmm_stream_t stream);
 bmm_status bmm_batched_plan_destroy(bmm_batched_plan plan);
+/* The base-case path (bmm_path, never AUTO) the plan runs. */
+bmm_status bmm_batched_plan_path(bmm_batched_plan plan, int32_t *path);
 
 /* ---- the steps of the path, exported for tests and experiments ---------- */
 

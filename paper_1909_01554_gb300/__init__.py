@@ -17,7 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbmm.so")
 
 OK, ERR_INVALID, ERR_ALIGN, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
-PATH_AUTO, PATH_TC_FP8, PATH_TC_I8, PATH_POPC, PATH_TC_FP8_PAIR = 0, 1, 2, 3, 4
+PATH_AUTO, PATH_TC_FP8, PATH_TC_I8, PATH_POPC, PATH_TC_FP8_PAIR, PATH_TC_FP4_PAIR = 0, 1, 2, 3, 4, 5
+TENSOR_PATHS = (PATH_TC_FP8, PATH_TC_FP8_PAIR, PATH_TC_FP4_PAIR)
 WINOGRAD, SELF_INVERSE, CHAINING = 0, 1, 2
 GF2, BOOL = 0, 1
 
@@ -28,7 +29,7 @@ EXPORTED = [
     "bmm_basis_change", "bmm_stream_status", "bmm_status_string", "bmm_last_cuda_error",
     "bmm_device_supported", "bmm_plan", "bmm_product_noalloc", "bmm_selftest_wait_timeout",
     "bmm_trace_enable", "bmm_trace_read", "bmm_launch_count", "bmm_autotune",
-    "bmm_autotune_clear",
+    "bmm_autotune_clear", "bmm_batched_plan_path", "bmm_batched_plan_create_ex",
 ]
 TUNE_MODEL = 1
 PHASE_BASE, PHASE_XOR, PHASE_TRANSPOSE = 0, 1, 2
@@ -90,10 +91,15 @@ def _lib_handle():
         L.bmm_batched_plan_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp,
                                               ctypes.POINTER(ctypes.c_void_p)]
         L.bmm_batched_plan_create.restype = i32
+        L.bmm_batched_plan_create_ex.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, i32,
+                                                 ctypes.POINTER(ctypes.c_void_p)]
+        L.bmm_batched_plan_create_ex.restype = i32
         L.bmm_batched_plan_run.argtypes = [vp, vp]
         L.bmm_batched_plan_run.restype = i32
         L.bmm_batched_plan_destroy.argtypes = [vp]
         L.bmm_batched_plan_destroy.restype = i32
+        L.bmm_batched_plan_path.argtypes = [vp, ctypes.POINTER(i32)]
+        L.bmm_batched_plan_path.restype = i32
         L.bmm_transpose.argtypes = [vp, vp, i64, i64, vp]
         L.bmm_transpose.restype = i32
         L.bmm_base_product.argtypes = [i32, i32, vp, vp, vp, i64, i64, i64, vp]
@@ -277,20 +283,28 @@ def batched(ops, As, Bs, Cs, ms, ks, ns, stream=None) -> None:
 
 
 class BatchedPlan:
-    """A reusable batch plan (see bmm_batched_plan_create); run() only launches."""
+    """A reusable batch plan (see bmm_batched_plan_create); run() only launches.
+    path: a bmm_path for every problem (default: the automatic choice)."""
 
-    def __init__(self, ops, As, Bs, Cs, ms, ks, ns):
+    def __init__(self, ops, As, Bs, Cs, ms, ks, ns, path: int = PATH_AUTO):
         if isinstance(ops, int):
             ops = [ops] * len(As)
         self._arr = _batch_arrays(ops, As, Bs, Cs, ms, ks, ns)
         h = ctypes.c_void_p(0)
-        _check(_lib_handle().bmm_batched_plan_create(*self._arr, ctypes.byref(h)),
-               "bmm_batched_plan_create")
+        _check(_lib_handle().bmm_batched_plan_create_ex(*self._arr, path, ctypes.byref(h)),
+               "bmm_batched_plan_create_ex")
         self._h = h
 
     def run(self, stream=None) -> None:
         _check(_lib_handle().bmm_batched_plan_run(self._h, _stream(stream)),
                "bmm_batched_plan_run")
+
+    def path(self) -> int:
+        """The base-case path the plan runs."""
+        p = ctypes.c_int32(0)
+        _check(_lib_handle().bmm_batched_plan_path(self._h, ctypes.byref(p)),
+               "bmm_batched_plan_path")
+        return p.value
 
     def destroy(self) -> None:
         if self._h:

@@ -20,9 +20,6 @@
 
 namespace bmm {
 
-bool tc_path_available();
-bool tc_pair_available();
-
 namespace {
 
 struct Key {
@@ -197,6 +194,7 @@ extern "C" bmm_status bmm_autotune(int32_t op, int64_t m, int64_t k, int64_t n, 
     // candidates the planner accepts, with their plans (serial depth by the
     // planner's memory rule)
     std::vector<int> paths;
+    if (tc_fp4_available()) paths.push_back(BMM_PATH_TC_FP4_PAIR);
     if (tc_pair_available()) paths.push_back(BMM_PATH_TC_FP8_PAIR);
     if (tc_path_available()) paths.push_back(BMM_PATH_TC_FP8);
     paths.push_back(BMM_PATH_POPC);

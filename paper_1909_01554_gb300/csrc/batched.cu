@@ -19,8 +19,6 @@
 
 namespace bmm {
 
-bool tc_path_available();
-
 namespace {
 
 constexpr int EPI_COST = 4;  // epilogue of one tile, in 128-bit k stages
@@ -69,6 +67,7 @@ struct bmm_batched_plan_s {
     int count = 0;
     bool tc = false;
     bool pair = false;  // SM pairs: 256-row tiles, one work list per CTA pair
+    bool fp4 = false;   // e2m1 operands (SM pairs only)
     // problem list (host)
     std::vector<int> op;
     std::vector<const uint64_t*> A, B;
@@ -92,10 +91,14 @@ struct bmm_batched_plan_s {
 
 namespace {
 
-bmm_status plan_build(bmm_batched_plan_s* P) {
+// path: the base case every problem runs on (resolved, never AUTO).
+bmm_status plan_build(bmm_batched_plan_s* P, int path) {
     const int count = P->count;
-    P->tc = tc_path_available();
-    const int pair_slots = P->tc ? tc_pair_slots() : 0;
+    P->tc = is_tc_path(path);
+    P->fp4 = path == BMM_PATH_TC_FP4_PAIR;
+    const int pair_slots =
+        path == BMM_PATH_TC_FP8 ? 0 : P->tc ? tc_pair_slots(P->fp4) : 0;
+    if (path != BMM_PATH_TC_FP8 && P->tc && pair_slots <= 0) return BMM_ERR_UNSUPPORTED;
     P->pair = pair_slots > 0;
     const int tile_m = P->pair ? 2 * TC_TILE_M : TC_TILE_M;
     // sizes of every device array
@@ -119,7 +122,10 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
     for (int i = 0; i < count; i++) {
         const int tm_n = (int)((P->m[i] + tile_m - 1) / tile_m);
         const int tn_n = (int)((P->n[i] + TC_TILE_N - 1) / TC_TILE_N);
-        const int nks = (int)((P->k[i] + TC_PACKED_BITS - 1) / TC_PACKED_BITS) * 2;
+        // cost: k in 128-bit units (the e2m1 form's stages carry twice the k
+        // for about the same time, as far as the tensor rate allows)
+        const int kstage = P->fp4 ? 512 : 256;
+        const int nks = (int)((P->k[i] + kstage - 1) / kstage) * 2;
         for (int a = 0; a < tm_n; a++)
             for (int b = 0; b < tn_n; b++) items.push_back({i, a, b, nks + EPI_COST});
     }
@@ -190,7 +196,7 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
         if (P->tc) {
             const int64_t kpad = P->kp[i] * 64;
             if (!tc_make_problem(&probs[i], Aop, lda, Bt, P->kp[i], P->C[i], P->n[i] / 64, P->m[i],
-                                 kpad, P->n[i], P->op[i], P->pair))
+                                 kpad, P->n[i], P->op[i], P->pair, P->fp4))
                 return BMM_ERR_CUDA;
         }
         tjobs[i] = {P->B[i], Bt, P->n[i] / 64, P->kp[i], P->k[i], P->n[i]};
@@ -233,7 +239,7 @@ bmm_status plan_run(bmm_batched_plan_s* P, cudaStream_t s) {
         BMM_CUDA_TRY(cudaGetLastError());
     }
     if (P->tc) {
-        BMM_CUDA_TRY(tc_launch_batched(P->d_probs, P->d_items, P->d_cta_ptr, P->grid, P->pair, s));
+        BMM_CUDA_TRY(tc_launch_batched(P->d_probs, P->d_items, P->d_cta_ptr, P->grid, P->pair, P->fp4, s));
         return BMM_OK;
     }
     // without tensor cores: the CUDA-core base case, one launch per problem
@@ -269,10 +275,21 @@ extern "C" {
 bmm_status bmm_batched_plan_create(int32_t count, const int32_t* ops, const uint64_t* const* A,
                                    const uint64_t* const* B, uint64_t* const* C, const int64_t* m,
                                    const int64_t* k, const int64_t* n, bmm_batched_plan* plan) {
+    return bmm_batched_plan_create_ex(count, ops, A, B, C, m, k, n, BMM_PATH_AUTO, plan);
+}
+
+bmm_status bmm_batched_plan_create_ex(int32_t count, const int32_t* ops,
+                                      const uint64_t* const* A, const uint64_t* const* B,
+                                      uint64_t* const* C, const int64_t* m, const int64_t* k,
+                                      const int64_t* n, int32_t path, bmm_batched_plan* plan) {
     if (!plan) return BMM_ERR_INVALID;
     *plan = nullptr;
+    if (path != BMM_PATH_AUTO && path != BMM_PATH_POPC && !is_tc_path(path))
+        return path == BMM_PATH_TC_I8 ? BMM_ERR_UNSUPPORTED : BMM_ERR_INVALID;
     bmm_status st = check_batch(count, ops, A, B, C, m, k, n);
     if (st != BMM_OK) return st;
+    if (path == BMM_PATH_AUTO) path = auto_path();
+    if (is_tc_path(path) && !tc_path_available()) return BMM_ERR_UNSUPPORTED;
     bmm_batched_plan_s* P = new bmm_batched_plan_s();
     cudaGetDevice(&P->device);
     P->count = count;
@@ -283,7 +300,7 @@ bmm_status bmm_batched_plan_create(int32_t count, const int32_t* ops, const uint
     P->m.assign(m, m + count);
     P->k.assign(k, k + count);
     P->n.assign(n, n + count);
-    st = plan_build(P);
+    st = plan_build(P, path);
     if (st != BMM_OK) {
         if (P->dmem) cudaFree(P->dmem);
         delete P;
@@ -296,6 +313,15 @@ bmm_status bmm_batched_plan_create(int32_t count, const int32_t* ops, const uint
 bmm_status bmm_batched_plan_run(bmm_batched_plan plan, bmm_stream_t stream) {
     if (!plan) return BMM_ERR_INVALID;
     return plan_run(plan, (cudaStream_t)stream);
+}
+
+bmm_status bmm_batched_plan_path(bmm_batched_plan plan, int32_t* path) {
+    if (!plan || !path) return BMM_ERR_INVALID;
+    *path = !plan->tc     ? BMM_PATH_POPC
+            : plan->fp4  ? BMM_PATH_TC_FP4_PAIR
+            : plan->pair ? BMM_PATH_TC_FP8_PAIR
+                         : BMM_PATH_TC_FP8;
+    return BMM_OK;
 }
 
 bmm_status bmm_batched_plan_destroy(bmm_batched_plan plan) {

@@ -40,6 +40,17 @@ int sm_count();
 // Compute capability major*10 + minor of the current device.
 int device_cc();
 
+// ---- base-case paths --------------------------------------------------------
+bool tc_path_available();  // tensor-core kernels: sm_103a and the TMA map encoder
+bool tc_pair_available();  // e4m3 operands on SM pairs (clusters of two)
+bool tc_fp4_available();   // e2m1 operands on SM pairs
+// The base-case path BMM_PATH_AUTO resolves to on the current device.
+int auto_path();
+inline bool is_tc_path(int path) {
+    return path == BMM_PATH_TC_FP8 || path == BMM_PATH_TC_FP8_PAIR ||
+           path == BMM_PATH_TC_FP4_PAIR;
+}
+
 // ---- launchers (each returns a launch error, or cudaSuccess) -------------
 cudaError_t launch_transpose(const uint64_t* X, uint64_t* Xt, int64_t rows, int64_t cols,
                              cudaStream_t s);

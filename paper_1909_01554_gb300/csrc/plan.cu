@@ -22,8 +22,6 @@ cudaError_t launch_combine(int operand, const uint64_t* X, int64_t pitch, int64_
                            uint32_t mask, uint64_t* dst, cudaStream_t s);
 cudaError_t launch_fold(const uint64_t* R, int64_t hr, int64_t hw, uint64_t* C, int64_t ldc,
                         uint32_t dest, uint32_t first, cudaStream_t s);
-bool tc_path_available();
-bool tc_pair_available();
 bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int64_t strideA,
                           const uint64_t* Bt, int64_t ldb, int64_t strideB, uint64_t* C,
                           int64_t ldc, int64_t strideC, int64_t count, int64_t m, int64_t k,
@@ -191,9 +189,9 @@ bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* op
     p.n = n;
     if (o.variant < 0 || o.variant > 2) return BMM_ERR_INVALID;
     p.variant = o.variant;
-    if (o.path < BMM_PATH_AUTO || o.path > BMM_PATH_TC_FP8_PAIR) return BMM_ERR_INVALID;
-    if (o.path != BMM_PATH_AUTO && o.path != BMM_PATH_POPC && !tc_path_available())
-        return BMM_ERR_UNSUPPORTED;
+    if (o.path < BMM_PATH_AUTO || o.path > BMM_PATH_TC_FP4_PAIR) return BMM_ERR_INVALID;
+    if (is_tc_path(o.path) && !tc_path_available()) return BMM_ERR_UNSUPPORTED;
+    if (o.path == BMM_PATH_TC_FP4_PAIR && !tc_fp4_available()) return BMM_ERR_UNSUPPORTED;
     // recursion depth
     if (op == OP_BOOL) {
         if (o.strassen_depth > 0) return BMM_ERR_INVALID;  // no additive inverse
@@ -221,20 +219,11 @@ bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* op
         p.depth = tdepth;
         o.path = tpath;
     }
-    // base-case path: the tensor cores wherever the device has them, as SM
-    // pairs where clusters can be launched (faster at every measured size
-    // from 4096^3 up), else the CUDA-core kernel. The tensor paths pad k
-    // (below) so that every leaf's k is a multiple of 128 bits.
-    if (o.path == BMM_PATH_AUTO) {
-        if (tc_path_available())
-            p.path = tc_pair_available() ? BMM_PATH_TC_FP8_PAIR : BMM_PATH_TC_FP8;
-        else
-            p.path = BMM_PATH_POPC;
-    } else {
-        p.path = o.path;
-    }
+    // base-case path (auto_path below); the tensor paths pad k so that every
+    // leaf's k is a multiple of 128 bits
+    p.path = o.path == BMM_PATH_AUTO ? auto_path() : o.path;
     p.kp = k;
-    if (p.path == BMM_PATH_TC_FP8 || p.path == BMM_PATH_TC_FP8_PAIR) {
+    if (is_tc_path(p.path)) {
         const int64_t unit = (int64_t)128 << p.depth;  // leaf k a multiple of 128 bits
         p.kp = (k + unit - 1) / unit * unit;
     }
@@ -322,6 +311,16 @@ bmm_status execute_plan(const Plan& p, const uint64_t* A, const uint64_t* B, uin
     }
     BMM_CUDA_TRY(launch_transpose_pitched(B, p.n / 64, ex.Bt, p.kp / 64, p.k, p.n, s));
     return ex.level(0, Aop, p.kp / 64, ex.Bt, p.kp / 64, C, p.n / 64, p.m, p.kp, p.n);
+}
+
+// Base case for BMM_PATH_AUTO: the tensor cores wherever the device has
+// them; on SM pairs where clusters can be launched (faster at every measured
+// size from 4096^3 up), with e2m1 operands (twice the e4m3 rate from 8192^3
+// up); else the CUDA-core kernel.
+int auto_path() {
+    if (!tc_path_available()) return BMM_PATH_POPC;
+    if (tc_fp4_available()) return BMM_PATH_TC_FP4_PAIR;
+    return tc_pair_available() ? BMM_PATH_TC_FP8_PAIR : BMM_PATH_TC_FP8;
 }
 
 bmm_status run_base_product(int op, int path, const uint64_t* A, int64_t lda, const uint64_t* Bt,

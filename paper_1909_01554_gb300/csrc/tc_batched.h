@@ -16,7 +16,7 @@ struct TcProblem {
     CUtensorMap mapB;  // Bt (n x k)
     uint64_t* C;
     int64_t ldc;       // words
-    int32_t m, n, nks, op;  // nks: 128-bit k stages, a multiple of 2
+    int32_t m, n, nks, op;  // nks: k stages (128 bits e4m3, 256 bits e2m1), a multiple of 2
 };
 
 // One output tile (TC_TILE_M rows, or 2 * TC_TILE_M for an SM pair, x
@@ -27,21 +27,21 @@ struct TcWorkItem {
 
 constexpr int TC_TILE_M = 128;
 constexpr int TC_TILE_N = 256;
-constexpr int TC_PACKED_BITS = 256;  // k granularity of the TMA stages
-
-// CTA pairs that can be resident at once (0: SM pairs unavailable).
-int tc_pair_slots();
+// CTA pairs of the e4m3 (fp4 false) or e2m1 kernel that can be resident at
+// once (0: SM pairs unavailable).
+int tc_pair_slots(bool fp4);
 
 // Fills the host copy of a problem descriptor (TMA maps need k % 128 == 0
-// and even pitches) for the single-SM or the SM-pair kernel. Returns false
-// if a map cannot be encoded.
+// and even pitches) for the single-SM or the SM-pair kernel, e4m3 or e2m1
+// operands (e2m1 only on SM pairs). Returns false if a map cannot be encoded.
 bool tc_make_problem(TcProblem* out, const uint64_t* A, int64_t lda, const uint64_t* Bt,
                      int64_t ldb, uint64_t* C, int64_t ldc, int64_t m, int64_t k, int64_t n,
-                     int op, bool pair);
+                     int op, bool pair, bool fp4);
 
 // One persistent launch over the per-unit work lists (unit_ptr has units + 1
 // entries); a unit is one CTA, or one CTA pair when `pair`.
 cudaError_t tc_launch_batched(const TcProblem* d_probs, const TcWorkItem* d_items,
-                              const int32_t* d_unit_ptr, int units, bool pair, cudaStream_t s);
+                              const int32_t* d_unit_ptr, int units, bool pair, bool fp4,
+                              cudaStream_t s);
 
 }  // namespace bmm

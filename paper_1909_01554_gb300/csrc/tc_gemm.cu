@@ -70,10 +70,8 @@ namespace {
 
 constexpr int BM = TC_TILE_M;    // rows of C per tile (UMMA M, TMEM lanes)
 constexpr int BN = TC_TILE_N;    // columns of C per tile (UMMA N)
-constexpr int KS = 128;          // k (bits) per operand stage
-constexpr int KP = TC_PACKED_BITS;  // k (bits) per packed (TMA) stage
-constexpr int SUB = KP / KS;     // operand stages per packed stage
-constexpr int MMA_K = 32;        // k per tcgen05.mma for 8-bit operands
+constexpr int SUB = 2;           // operand stages per packed stage
+constexpr int KS_MIN = 128;      // k granularity of the operands (both formats)
 // 18 warps: an SM sub-partition (16 K registers) holds at most five of
 // them, which leaves 96 registers per thread (the A expansion keeps 64
 // output words live for one wide TMEM store). Warps 0..15 are split between
@@ -89,9 +87,17 @@ constexpr int THREADS = 18 * 32;
 // L2 (measured: 64 row-tiles no longer fit and A is re-read).
 constexpr int GROUP_M = 32;
 
+// An operand stage is 128 bytes of expanded operand per row in both
+// formats: 128 k as e4m3 bytes, or 256 k as e2m1 nibbles (two per byte).
+// One tcgen05.mma consumes 32 bytes of k per row (K = 32 e4m3, K = 64 e2m1),
+// so the descriptors and TMEM columns advance the same way in both.
 constexpr int ACC_COL = 0;               // accumulator: TMEM columns [0, BN)
-constexpr int A_COL = BN;                // A ring: columns [BN, BN + ESTAGES * KS / 4)
-constexpr int A_STAGE_COLS = KS / 4;     // 4 e4m3 per 32-bit column
+constexpr int A_COL = BN;                // A ring: columns [BN, BN + ESTAGES * A_STAGE_COLS)
+constexpr int A_STAGE_COLS = 32;         // 128 bytes of a row = 32 columns of 32 bits
+constexpr int A_MMA_COLS = 8;            // 32 bytes of a row per MMA
+constexpr int MMAS_PER_STAGE = 4;
+constexpr int SF_COL = 448;              // e2m1: block scales, columns [448, 512)
+constexpr int SF_COLS = 64;
 constexpr int TMEM_COLS = 512;
 
 // Per-CTA shapes and shared-memory layout. A CTA always owns 128 rows of C
@@ -101,12 +107,16 @@ constexpr int TMEM_COLS = 512;
 // each CTA expands only its half of the Bt rows, and the pair's MMAs read
 // both halves: per SM, half the shared-memory traffic and a third less
 // expansion work for the same number of MACs.
-template <bool PAIR>
+template <bool PAIR, bool FP4>
 struct Lay {
+    static constexpr int KS = FP4 ? 256 : 128;  // k (bits) per operand stage
+    static constexpr int KP = SUB * KS;         // k (bits) per packed (TMA) stage
+    static constexpr int MMA_K = FP4 ? 64 : 32; // k per tcgen05.mma
     // ring depths: packed stages (shared) and operand stages (Bt in shared,
-    // A in TMEM); a pair's smaller operand stages leave room for deeper rings
+    // A in TMEM); a pair's smaller operand stages leave room for deeper rings.
+    // The e2m1 form gives up two operand stages of TMEM to the block scales.
     static constexpr int PSTAGES = PAIR ? 6 : 4;
-    static constexpr int ESTAGES = PAIR ? 8 : 4;
+    static constexpr int ESTAGES = PAIR ? (FP4 ? 6 : 8) : 4;
     // operand slots: the two operand stages one packed stage fills
     static constexpr int OSLOTS = ESTAGES / SUB;
     // packed stages the MMA issuer covers with one wait (needs more slots
@@ -125,9 +135,9 @@ struct Lay {
                   "warp % 4 is the TMEM lane quarter");
     static constexpr int TILE_M = PAIR ? 2 * BM : BM;  // rows of C per tile
     static constexpr int BROWS = PAIR ? BN / 2 : BN;   // Bt rows held by one CTA
-    static constexpr int PA_BYTES = BM * KP / 8;       // 4 KB packed A per packed stage
+    static constexpr int PA_BYTES = BM * KP / 8;       // packed A per packed stage
     static constexpr int PB_BYTES = BROWS * KP / 8;    // packed Bt per packed stage
-    static constexpr int EB_BYTES = BROWS * KS;        // expanded Bt per operand stage
+    static constexpr int EB_BYTES = BROWS * 128;       // expanded Bt per operand stage
     static constexpr int OFF_EB = 0;
     static constexpr int OFF_PA = OFF_EB + ESTAGES * EB_BYTES;
     static constexpr int OFF_PB = OFF_PA + PSTAGES * PA_BYTES;
@@ -135,7 +145,10 @@ struct Lay {
     static constexpr int OFF_TMEM_SLOT = OFF_BAR + NBARS * 8;
     static constexpr int SMEM_BYTES = OFF_TMEM_SLOT + 16 + 1024;  // + alignment slack
     static_assert(EB_BYTES % 1024 == 0, "swizzle atoms stay 1024-byte aligned");
-    static_assert(A_COL + ESTAGES * A_STAGE_COLS <= TMEM_COLS, "TMEM budget");
+    static_assert(A_COL + ESTAGES * A_STAGE_COLS <= (FP4 ? SF_COL : TMEM_COLS), "TMEM budget");
+    static_assert(SF_COL + SF_COLS <= TMEM_COLS, "TMEM budget");
+    static_assert(KS / MMA_K == MMAS_PER_STAGE && MMA_K * (FP4 ? 4 : 8) == 32 * A_MMA_COLS,
+                  "an MMA reads 32 bytes of k per row");
     static_assert(ESTAGES % SUB == 0, "a packed stage's operand stages are adjacent in TMEM");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
 };
@@ -276,6 +289,16 @@ __host__ __device__ constexpr uint32_t instr_desc(uint32_t dfmt) {
     return (dfmt << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor for kind::mxf4 (block-scaled e2m1, FP32
+// accumulate): A and B format 1 (E2M1) at bits 7 and 10, both K-major,
+// N >> 3 at bit 17, scale format 1 (UE8M0) at bit 23, M >> 4 at bit 24;
+// scale-factor data ids 0 and K = 64 (bit 31 clear).
+template <int M>
+__host__ __device__ constexpr uint32_t instr_desc_mxf4() {
+    return (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | (1u << 23) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
 // D (TMEM) += A (TMEM) x B (shared, descriptor). PAIR: cta_group::2, issued
 // by the even CTA of the pair; A, B and D are the two CTAs' halves at the
 // same TMEM / shared-memory addresses.
@@ -295,6 +318,31 @@ __device__ __forceinline__ void mma_f8_ta(uint32_t tmem_d, uint32_t tmem_a, uint
             "setp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
             "r"(tmem_a), "l"(db), "r"(idesc), "r"(accumulate)
+            : "memory");
+}
+
+// As mma_f8_ta for e2m1 operands with block scales: every 32 k of a row of
+// A (B) is scaled by the UE8M0 byte the tensor core reads from TMEM at
+// tmem_sfa (tmem_sfb); here every scale byte holds the same value.
+template <bool PAIR>
+__device__ __forceinline__ void mma_f4_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t db,
+                                          uint32_t idesc, uint32_t tmem_sfa, uint32_t tmem_sfb,
+                                          uint32_t accumulate) {
+    if (PAIR)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %6, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X"
+            " [%0], [%1], %2, %3, [%4], [%5], p;\n\t}" ::"r"(tmem_d),
+            "r"(tmem_a), "l"(db), "r"(idesc), "r"(tmem_sfa), "r"(tmem_sfb), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %6, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X"
+            " [%0], [%1], %2, %3, [%4], [%5], p;\n\t}" ::"r"(tmem_d),
+            "r"(tmem_a), "l"(db), "r"(idesc), "r"(tmem_sfa), "r"(tmem_sfb), "r"(accumulate)
             : "memory");
 }
 
@@ -397,6 +445,7 @@ __device__ __forceinline__ void tmem_st64(uint32_t taddr, const uint32_t (&v)[64
 // on the FMA pipe and leave the integer pipe the masks alone.
 struct Spread {
     uint32_t f[8];  // f[j]: 2^(3-j) for j <= 3 (low product), 2^(35-j) for j > 3 (high)
+    uint32_t g[4];  // spread4: 2, 1 (low products), 2^31, 2^30 (high)
 };
 
 __device__ __forceinline__ void spread8(uint32_t x, const Spread& sp, uint32_t* y) {
@@ -410,6 +459,20 @@ __device__ __forceinline__ void spread8(uint32_t x, const Spread& sp, uint32_t* 
     y[6] = __umulhi(x, sp.f[6]) & mask;
     y[7] = __umulhi(x, sp.f[7]) & mask;
 }
+
+// e2m1 form: output word j (j = 0..3) gets bit (4t + j) of x in nibble t,
+// moved to bit 1 of the nibble (e2m1 0x2 = 1.0, scaled by 2^-6 at the MMA,
+// so products are 2^-12 as in the e4m3 form).
+__device__ __forceinline__ void spread4(uint32_t x, const Spread& sp, uint32_t* y) {
+    constexpr uint32_t mask = 0x22222222u;
+    y[0] = (x * sp.g[0]) & mask;
+    y[1] = x & mask;
+    y[2] = __umulhi(x, sp.g[2]) & mask;
+    y[3] = __umulhi(x, sp.g[3]) & mask;
+}
+
+// UE8M0 block scale 2^-6 (biased exponent 121) in every byte.
+constexpr uint32_t SCALE_WORD = 0x79797979u;
 
 // 32 result bits of one accumulator row slice -> one word, bit j from v[j].
 // GF(2): v[j] = count * 2^-12 exactly; adding 2^11 puts count's LSB in bit 0.
@@ -536,12 +599,12 @@ __device__ __forceinline__ int tile_nks(const Params& p, int idx) {
     return p.nks;
 }
 
-template <bool BATCHED, bool PAIR>
+template <bool BATCHED, bool PAIR, bool FP4>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const Params p) {
-    using LY = Lay<PAIR>;
-    constexpr int PSTAGES = LY::PSTAGES, OSLOTS = LY::OSLOTS;
+    using LY = Lay<PAIR, FP4>;
+    constexpr int PSTAGES = LY::PSTAGES, OSLOTS = LY::OSLOTS, KP = LY::KP;
     constexpr int BEXP_WARPS = LY::BEXP_WARPS, EPI_WARP0 = LY::EPI_WARP0,
                   EPI_WARPS = LY::EPI_WARPS;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -629,6 +692,42 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (!mbar_wait(full_p(i % PSTAGES), (i / PSTAGES) & 1, p.err)) break;
             }
         }
+    } else if (FP4 && warp < BEXP_WARPS) {
+        // ---------------------------------------------------- Bt expansion, e2m1
+        // Per packed stage: items of 2 rows x 16 packed words (both operand
+        // stages). Lane = (half h, row rr of the item, word wl of the half):
+        // word w = 8h + wl goes to 16-byte chunk wl of operand stage 2q + h.
+        // A quarter-warp holds the 8 chunks of one row: 8 distinct bank groups.
+        const int h = lane >> 4, rr = (lane >> 3) & 1, wl = lane & 7;
+        const Spread sp = p.sp;
+        for (int pit = 0; pit < total_pit; pit++) {
+            const int s = pit % PSTAGES;
+            const int q = pit % OSLOTS;
+            if (!mbar_wait(full_p(s), (pit / PSTAGES) & 1, p.err) ||
+                !mbar_wait(empty_o(q), ((pit / OSLOTS) & 1) ^ 1, p.err))
+                break;
+            constexpr int ITEMS = (LY::BROWS / 2) / BEXP_WARPS;
+            const uint32_t* pb =
+                reinterpret_cast<const uint32_t*>(smem + LY::OFF_PB + s * LY::PB_BYTES);
+            uint8_t* eb = smem + LY::OFF_EB + (2 * q + h) * LY::EB_BYTES;
+            uint32_t x[ITEMS];
+#pragma unroll
+            for (int i = 0; i < ITEMS; i++)
+                x[i] = pb[((warp + BEXP_WARPS * i) * 2 + rr) * 16 + 8 * h + wl];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty_p(s));
+#pragma unroll
+            for (int i = 0; i < ITEMS; i++) {
+                const int row = (warp + BEXP_WARPS * i) * 2 + rr;
+                uint32_t y[4];
+                spread4(x[i], sp, y);
+                *reinterpret_cast<uint4*>(eb + row * 128 + ((wl ^ (row & 7)) * 16)) =
+                    make_uint4(y[0], y[1], y[2], y[3]);
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) arrive_leader(full_o(q));
+        }
     } else if (warp < BEXP_WARPS) {
         // ---------------------------------------------------- Bt expansion (shared)
         // Per packed stage: items of 4 rows x 8 packed words (both operand
@@ -680,26 +779,43 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int row = 32 * quarter + lane;
         const Spread sp = p.sp;
         const uint32_t tlane = (uint32_t)(32 * quarter) << 16;
+        if (FP4) {
+            // block scales for this lane quarter, before the first full_o arrive
+            uint32_t f[64];
+#pragma unroll
+            for (int i = 0; i < 64; i++) f[i] = SCALE_WORD;
+            tmem_st64(tmem + tlane + (uint32_t)SF_COL, f);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
         for (int pit = 0; pit < total_pit; pit++) {
             const int s = pit % PSTAGES;
             const int q = pit % OSLOTS;
             if (!mbar_wait(full_p(s), (pit / PSTAGES) & 1, p.err)) break;
             const uint4* src = reinterpret_cast<const uint4*>(smem + LY::OFF_PA +
                                                               s * LY::PA_BYTES + row * (KP / 8));
-            const uint4 xa = src[0], xb = src[1];
+            constexpr int NV = KP / 128;  // 16-byte vectors per packed row
+            uint4 xv[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++) xv[v] = src[v];
             __syncwarp();
             if (lane == 0) mbar_arrive(empty_p(s));
             if (!mbar_wait(empty_o(q), ((pit / OSLOTS) & 1) ^ 1, p.err)) break;
             tc_fence_after();  // the slot's MMAs (seen complete) before our TMEM stores
             uint32_t y[64];
-            spread8(xa.x, sp, y);
-            spread8(xa.y, sp, y + 8);
-            spread8(xa.z, sp, y + 16);
-            spread8(xa.w, sp, y + 24);
-            spread8(xb.x, sp, y + 32);
-            spread8(xb.y, sp, y + 40);
-            spread8(xb.z, sp, y + 48);
-            spread8(xb.w, sp, y + 56);
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                if (FP4) {
+                    spread4(xv[v].x, sp, y + 16 * v);
+                    spread4(xv[v].y, sp, y + 16 * v + 4);
+                    spread4(xv[v].z, sp, y + 16 * v + 8);
+                    spread4(xv[v].w, sp, y + 16 * v + 12);
+                } else {
+                    spread8(xv[v].x, sp, y + 32 * v);
+                    spread8(xv[v].y, sp, y + 32 * v + 8);
+                    spread8(xv[v].z, sp, y + 32 * v + 16);
+                    spread8(xv[v].w, sp, y + 32 * v + 24);
+                }
+            }
             tmem_st64(tmem + tlane + (uint32_t)(A_COL + 2 * q * A_STAGE_COLS), y);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
@@ -709,7 +825,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (warp == MMA_WARP) {
         // ---------------------------------------------------- MMA issuer
         if (lane == 0 && rank == 0) {
-            constexpr uint32_t idesc = instr_desc<LY::TILE_M>(1u);
+            constexpr uint32_t idesc =
+                FP4 ? instr_desc_mxf4<LY::TILE_M>() : instr_desc<LY::TILE_M>(1u);
             // operand stage e's descriptor: the start-address field (bytes >> 4)
             // moves by EB_BYTES >> 4 per stage; every stage lies below 256 KB,
             // so no carry
@@ -747,9 +864,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                         const uint32_t ta = tmem + (uint32_t)(A_COL + e * A_STAGE_COLS);
                         const uint64_t db = db_base + (uint64_t)(e * (LY::EB_BYTES >> 4));
 #pragma unroll
-                        for (int j = 0; j < KS / MMA_K; j++)
-                            mma_f8_ta<PAIR>(tmem + ACC_COL, ta + j * (MMA_K / 4), db + 2 * j, idesc,
-                                            (kin > 0 || sub > 0 || j > 0) ? 1u : 0u);
+                        for (int j = 0; j < MMAS_PER_STAGE; j++) {
+                            const uint32_t acc = (kin > 0 || sub > 0 || j > 0) ? 1u : 0u;
+                            if (FP4)
+                                mma_f4_ta<PAIR>(tmem + ACC_COL, ta + j * A_MMA_COLS, db + 2 * j,
+                                                idesc, tmem + SF_COL, tmem + SF_COL + SF_COLS / 2,
+                                                acc);
+                            else
+                                mma_f8_ta<PAIR>(tmem + ACC_COL, ta + j * A_MMA_COLS, db + 2 * j,
+                                                idesc, acc);
+                        }
                     }
                     mma_commit<PAIR>(empty_o(q));
                     kin += SUB;
@@ -849,17 +973,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 3-D map over uint64 words: (k/64 words, rows, leaves), box (KP/64, box_rows, 1).
-// Boxes that run past k or the rows are zero-filled, which adds nothing to
-// the counts.
+// 3-D map over uint64 words: (k/64 words, rows, leaves), box (box_words,
+// box_rows, 1). Boxes that run past k or the rows are zero-filled, which
+// adds nothing to the counts.
 bool make_map(CUtensorMap* map, const uint64_t* base, int64_t kwords, int64_t rows,
-              int64_t pitch, int64_t count, int64_t stride, int box_rows) {
+              int64_t pitch, int64_t count, int64_t stride, int box_rows, int box_words) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[3] = {(cuuint64_t)kwords, (cuuint64_t)rows, (cuuint64_t)count};
     const int64_t leaf_stride = count > 1 ? stride : rows * pitch;
     cuuint64_t strides[2] = {(cuuint64_t)(pitch * 8), (cuuint64_t)(leaf_stride * 8)};
-    cuuint32_t box[3] = {(cuuint32_t)(KP / 64), (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)box_words, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void*)base, dims, strides, box,
                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -878,7 +1002,7 @@ int current_device() {
 // Per-device one-time setup (function attributes and occupancy are per device).
 std::mutex g_setup_mu;
 
-template <bool BATCHED, bool PAIR>
+template <bool BATCHED, bool PAIR, bool FP4>
 cudaError_t set_smem_attr() {
     static bool done[MAX_DEVICES] = {false};
     static cudaError_t err[MAX_DEVICES];
@@ -886,37 +1010,46 @@ cudaError_t set_smem_attr() {
     if (d < 0 || d >= MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_setup_mu);
     if (!done[d]) {
-        err[d] = cudaFuncSetAttribute(tc_nt_kernel<BATCHED, PAIR>,
+        err[d] = cudaFuncSetAttribute(tc_nt_kernel<BATCHED, PAIR, FP4>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      Lay<PAIR>::SMEM_BYTES);
+                                      Lay<PAIR, FP4>::SMEM_BYTES);
         done[d] = true;
     }
     return err[d];
 }
 
-// CTA pairs that can be resident at once on the current device (clusters of
-// two on one TPC); 0 if cluster launches are unavailable.
+cudaLaunchConfig_t pair_config(unsigned units, size_t smem, cudaLaunchAttribute* at) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * units);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = smem;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// CTA pairs of the e4m3 (FP4 false) or e2m1 kernel that can be resident at
+// once on the current device (clusters of two on one TPC); 0 if cluster
+// launches are unavailable.
+template <bool FP4>
 int pair_slots() {
     static int slots[MAX_DEVICES];
     static bool done[MAX_DEVICES] = {false};
     const int d = current_device();
     if (d < 0 || d >= MAX_DEVICES) return 0;
-    if (set_smem_attr<false, true>() != cudaSuccess) return 0;
+    if (set_smem_attr<false, true, FP4>() != cudaSuccess) return 0;
     std::lock_guard<std::mutex> lk(g_setup_mu);
     if (!done[d]) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(2 * (unsigned)sm_count());
-        cfg.blockDim = dim3(THREADS);
-        cfg.dynamicSmemBytes = Lay<true>::SMEM_BYTES;
         cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
+        const cudaLaunchConfig_t cfg =
+            pair_config((unsigned)sm_count(), Lay<true, FP4>::SMEM_BYTES, at);
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, tc_nt_kernel<false, true>, &cfg) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveClusters(&n, tc_nt_kernel<false, true, FP4>, &cfg) !=
+            cudaSuccess) {
             (void)cudaGetLastError();
             n = 0;
         }
@@ -927,73 +1060,77 @@ int pair_slots() {
 }
 
 // units: CTAs (single) or CTA pairs (PAIR) to launch.
-template <bool BATCHED, bool PAIR>
+template <bool BATCHED, bool PAIR, bool FP4>
 cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const Params& prm, int units,
                       cudaStream_t s) {
-    const cudaError_t e = set_smem_attr<BATCHED, PAIR>();
+    static_assert(PAIR || !FP4, "the e2m1 form runs on SM pairs");
+    const cudaError_t e = set_smem_attr<BATCHED, PAIR, FP4>();
     if (e != cudaSuccess) return e;
     if (!PAIR) {
-        tc_nt_kernel<BATCHED, false><<<units, THREADS, Lay<false>::SMEM_BYTES, s>>>(ma, mb, prm);
+        tc_nt_kernel<BATCHED, false, false>
+            <<<units, THREADS, Lay<false, false>::SMEM_BYTES, s>>>(ma, mb, prm);
         return cudaGetLastError();
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * (unsigned)units);
-    cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = Lay<PAIR>::SMEM_BYTES;
-    cfg.stream = s;
     cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, tc_nt_kernel<BATCHED, PAIR>, ma, mb, prm);
+    cudaLaunchConfig_t cfg = pair_config((unsigned)units, Lay<PAIR, FP4>::SMEM_BYTES, at);
+    cfg.stream = s;
+    return cudaLaunchKernelEx(&cfg, tc_nt_kernel<BATCHED, PAIR, FP4>, ma, mb, prm);
 }
 
 Spread spread_factors() {
     Spread sp;
     for (int j = 0; j < 8; j++) sp.f[j] = j <= 3 ? (1u << (3 - j)) : (1u << (35 - j));
+    sp.g[0] = 2u;
+    sp.g[1] = 1u;
+    sp.g[2] = 1u << 31;
+    sp.g[3] = 1u << 30;
     return sp;
 }
+
+// k bits per operand stage of a tensor path.
+int64_t stage_bits(int path) { return path == BMM_PATH_TC_FP4_PAIR ? 256 : 128; }
 
 }  // namespace
 
 bool tc_path_available() { return device_cc() == 103 && encode_fn() != nullptr; }
 
 // SM pairs need cluster launches with both CTAs of a pair resident at once.
-bool tc_pair_available() { return tc_path_available() && pair_slots() > 0; }
+bool tc_pair_available() { return tc_path_available() && pair_slots<false>() > 0; }
+bool tc_fp4_available() { return tc_path_available() && pair_slots<true>() > 0; }
 
 // Longest run of k stages accumulated before the counts are flushed from
-// TMEM: the e4m3 path reads parity through an FP32 value count * 2^-12,
-// exact while count < 2^23 (at most 65534 stages of 128); S32 needs none.
+// TMEM: both formats read parity through an FP32 value count * 2^-12, exact
+// while count < 2^23: at most 65534 stages of 128 k, or 32766 of 256.
 int tc_kchunk_stages(int path, int nks) {
     // a multiple of the operand stages per packed stage (flushes happen between packed stages)
-    const int cap = 65534;
-    if (path == BMM_PATH_TC_FP8 || path == BMM_PATH_TC_FP8_PAIR) return nks < cap ? nks : cap;
-    return nks;
+    const int cap = path == BMM_PATH_TC_FP4_PAIR ? 32766 : 65534;
+    return nks < cap ? nks : cap;
 }
 
 bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int64_t strideA,
                           const uint64_t* Bt, int64_t ldb, int64_t strideB, uint64_t* C,
                           int64_t ldc, int64_t strideC, int64_t count, int64_t m, int64_t k,
                           int64_t n, cudaStream_t s) {
-    const bool pair = path == BMM_PATH_TC_FP8_PAIR;
+    const bool fp4 = path == BMM_PATH_TC_FP4_PAIR;
+    const bool pair = fp4 || path == BMM_PATH_TC_FP8_PAIR;
     if (!tc_path_available() || (path != BMM_PATH_TC_FP8 && !pair)) return BMM_ERR_UNSUPPORTED;
-    if (k % KS || (lda & 1) || (ldb & 1) || (count > 1 && ((strideA & 1) || (strideB & 1))))
+    if (k % KS_MIN || (lda & 1) || (ldb & 1) ||
+        (count > 1 && ((strideA & 1) || (strideB & 1))))
         return BMM_ERR_UNSUPPORTED;
     if (m <= 0 || n <= 0 || k <= 0 || count <= 0) return BMM_OK;
     // tile and stage indices are 32-bit in the kernel
-    if (m > 0x7fffffffLL || n > 0x7fffffffLL || k / KS > 0x3fffffffLL) return BMM_ERR_UNSUPPORTED;
-    const int slots = pair ? pair_slots() : sm_count();
+    if (m > 0x7fffffffLL || n > 0x7fffffffLL || k / KS_MIN > 0x3fffffffLL)
+        return BMM_ERR_UNSUPPORTED;
+    const int slots = fp4 ? pair_slots<true>() : pair ? pair_slots<false>() : sm_count();
     if (slots <= 0) return BMM_ERR_UNSUPPORTED;
     uint32_t* err = device_error_word();
     if (!err) return BMM_ERR_NOMEM;
-    const int tile_m = pair ? Lay<true>::TILE_M : Lay<false>::TILE_M;
-    const int brows = pair ? Lay<true>::BROWS : Lay<false>::BROWS;
+    const int64_t kp = SUB * stage_bits(path);  // k bits per packed stage
+    const int tile_m = pair ? Lay<true, false>::TILE_M : Lay<false, false>::TILE_M;
+    const int brows = pair ? Lay<true, false>::BROWS : Lay<false, false>::BROWS;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, A, k / 64, m, lda, count, strideA, BM) ||
-        !make_map(&mb, Bt, k / 64, n, ldb, count, strideB, brows))
+    if (!make_map(&ma, A, k / 64, m, lda, count, strideA, BM, (int)(kp / 64)) ||
+        !make_map(&mb, Bt, k / 64, n, ldb, count, strideB, brows, (int)(kp / 64)))
         return BMM_ERR_CUDA;
     Params prm{};
     prm.C = C;
@@ -1001,7 +1138,7 @@ bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int6
     prm.strideC = strideC;
     prm.m = (int)m;
     prm.n = (int)n;
-    prm.nks = (int)((k + KP - 1) / KP) * SUB;  // whole packed stages; the tail is zero-filled
+    prm.nks = (int)((k + kp - 1) / kp) * SUB;  // whole packed stages; the tail is zero-filled
     prm.op = op;
     prm.kchunk = tc_kchunk_stages(path, prm.nks);
     prm.tiles_m = (int)((m + tile_m - 1) / tile_m);
@@ -1013,8 +1150,9 @@ bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int6
     prm.sp = spread_factors();
     TraceScope ts(BMM_PHASE_BASE, s);
     const int units = prm.total_tiles < slots ? prm.total_tiles : slots;
-    const cudaError_t e = pair ? launch_tc<false, true>(ma, mb, prm, units, s)
-                               : launch_tc<false, false>(ma, mb, prm, units, s);
+    const cudaError_t e = fp4    ? launch_tc<false, true, true>(ma, mb, prm, units, s)
+                          : pair ? launch_tc<false, true, false>(ma, mb, prm, units, s)
+                                 : launch_tc<false, false, false>(ma, mb, prm, units, s);
     if (e != cudaSuccess) return cuda_fail(e);
     return BMM_OK;
 }
@@ -1023,41 +1161,52 @@ bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int6
 
 namespace bmm {
 
-int tc_pair_slots() { return tc_path_available() ? pair_slots() : 0; }
+int tc_pair_slots(bool fp4) {
+    if (!tc_path_available()) return 0;
+    return fp4 ? pair_slots<true>() : pair_slots<false>();
+}
 
 bool tc_make_problem(TcProblem* out, const uint64_t* A, int64_t lda, const uint64_t* Bt,
                      int64_t ldb, uint64_t* C, int64_t ldc, int64_t m, int64_t k, int64_t n,
-                     int op, bool pair) {
-    if (k % KS || (lda & 1) || (ldb & 1)) return false;
-    if (!make_map(&out->mapA, A, k / 64, m, lda, 1, 0, BM) ||
+                     int op, bool pair, bool fp4) {
+    if (k % KS_MIN || (lda & 1) || (ldb & 1) || (fp4 && !pair)) return false;
+    const int64_t kp = SUB * stage_bits(fp4 ? BMM_PATH_TC_FP4_PAIR : BMM_PATH_TC_FP8);
+    if (!make_map(&out->mapA, A, k / 64, m, lda, 1, 0, BM, (int)(kp / 64)) ||
         !make_map(&out->mapB, Bt, k / 64, n, ldb, 1, 0,
-                  pair ? Lay<true>::BROWS : Lay<false>::BROWS))
+                  pair ? Lay<true, false>::BROWS : Lay<false, false>::BROWS, (int)(kp / 64)))
         return false;
     out->C = C;
     out->ldc = ldc;
     out->m = (int32_t)m;
     out->n = (int32_t)n;
-    out->nks = (int32_t)(((k + KP - 1) / KP) * SUB);
+    out->nks = (int32_t)(((k + kp - 1) / kp) * SUB);
     out->op = op;
     return true;
 }
 
+int tc_problem_kchunk(bool fp4) {
+    return tc_kchunk_stages(fp4 ? BMM_PATH_TC_FP4_PAIR : BMM_PATH_TC_FP8, 0x7fffffff);
+}
+
 cudaError_t tc_launch_batched(const TcProblem* d_probs, const TcWorkItem* d_items,
-                              const int32_t* d_unit_ptr, int units, bool pair, cudaStream_t s) {
+                              const int32_t* d_unit_ptr, int units, bool pair, bool fp4,
+                              cudaStream_t s) {
+    if (fp4 && !pair) return cudaErrorInvalidValue;
     uint32_t* err = device_error_word();
     if (!err) return cudaErrorMemoryAllocation;
     Params prm{};
     prm.probs = d_probs;
     prm.items = d_items;
     prm.cta_ptr = d_unit_ptr;
-    prm.kchunk = 65534;
+    prm.kchunk = tc_problem_kchunk(fp4);
     prm.err = err;
     prm.sp = spread_factors();
     CUtensorMap dummy;
     std::memset(&dummy, 0, sizeof(dummy));
     TraceScope ts(BMM_PHASE_BASE, s);
-    return pair ? launch_tc<true, true>(dummy, dummy, prm, units, s)
-                : launch_tc<true, false>(dummy, dummy, prm, units, s);
+    return fp4    ? launch_tc<true, true, true>(dummy, dummy, prm, units, s)
+           : pair ? launch_tc<true, true, false>(dummy, dummy, prm, units, s)
+                  : launch_tc<true, false, false>(dummy, dummy, prm, units, s);
 }
 
 }  // namespace bmm

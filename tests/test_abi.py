@@ -84,3 +84,31 @@ def test_autotune_argument_checks_need_no_gpu(built_lib):
     assert L.bmm_autotune(0, 64, 64, 64, 4, None, ctypes.byref(r)) == bmm.ERR_INVALID
     assert L.bmm_autotune(0, 64, 64, 64, 0, None, None) == bmm.ERR_INVALID
     L.bmm_autotune_clear()
+
+
+def test_batched_plan_argument_checks_need_no_gpu(built_lib):
+    """A batch plan rejects an unknown base-case path, a null plan pointer and
+    bad problem sizes before any CUDA call; the 8-bit integer path does not
+    exist on sm_103a."""
+    import ctypes
+
+    import paper_1909_01554_gb300 as bmm
+
+    L = bmm.lib()
+    one = lambda t, v: (t * 1)(v)  # noqa: E731
+    ops = one(ctypes.c_int32, 0)
+    ptr = one(ctypes.c_void_p, 1 << 20)
+    sz = one(ctypes.c_int64, 64)
+    bad = one(ctypes.c_int64, 96)
+    h = ctypes.c_void_p(0)
+    args = (1, ops, ptr, ptr, ptr, sz, sz, sz)
+    assert L.bmm_batched_plan_create_ex(*args, 99, ctypes.byref(h)) == bmm.ERR_INVALID
+    assert L.bmm_batched_plan_create_ex(*args, -1, ctypes.byref(h)) == bmm.ERR_INVALID
+    assert L.bmm_batched_plan_create_ex(*args, bmm.PATH_TC_I8,
+                                        ctypes.byref(h)) == bmm.ERR_UNSUPPORTED
+    assert L.bmm_batched_plan_create_ex(*args, bmm.PATH_AUTO, None) == bmm.ERR_INVALID
+    assert L.bmm_batched_plan_create_ex(1, ops, ptr, ptr, ptr, bad, sz, sz, bmm.PATH_AUTO,
+                                        ctypes.byref(h)) == bmm.ERR_INVALID
+    assert h.value is None
+    p = ctypes.c_int32(0)
+    assert L.bmm_batched_plan_path(None, ctypes.byref(p)) == bmm.ERR_INVALID

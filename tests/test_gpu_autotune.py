@@ -13,7 +13,7 @@ if not torch.cuda.is_available():  # pragma: no cover - CPU machine
 
 import paper_1909_01554_gb300 as bmm  # noqa: E402
 
-VALID_PATHS = {bmm.PATH_TC_FP8, bmm.PATH_TC_FP8_PAIR, bmm.PATH_POPC}
+VALID_PATHS = {*bmm.TENSOR_PATHS, bmm.PATH_POPC}
 
 
 def product_matches(op, m, k, n, seed):
@@ -58,5 +58,5 @@ def test_tensor_cores_beat_cuda_cores_on_a_large_cubic_shape():
     bmm.autotune_clear()
     for model in (False, True):
         r = bmm.autotune(bmm.BOOL, 16384, 16384, 16384, model=model)
-        assert r["path"] in (bmm.PATH_TC_FP8, bmm.PATH_TC_FP8_PAIR)
+        assert r["path"] in bmm.TENSOR_PATHS
     bmm.autotune_clear()

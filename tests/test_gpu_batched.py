@@ -57,6 +57,36 @@ def test_batched_mixed_small():
     check_all(SMALL, host, dev)
 
 
+@pytest.mark.parametrize("path", [bmm.PATH_POPC, *bmm.TENSOR_PATHS])
+def test_batched_plan_on_each_path(path):
+    """The same uneven batch through a plan on every base case (the automatic
+    choice takes the fastest; the others stay reachable and exact)."""
+    if path != bmm.PATH_POPC and not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    host, dev = make_batch(SMALL, 43)
+    ops = [s[3] for s in SMALL]
+    plan = bmm.BatchedPlan(ops, [d[0] for d in dev], [d[1] for d in dev], [d[2] for d in dev],
+                           [s[0] for s in SMALL], [s[1] for s in SMALL], [s[2] for s in SMALL],
+                           path=path)
+    assert plan.path() == path
+    plan.run()
+    bmm.stream_status()
+    plan.destroy()
+    check_all(SMALL, host, dev)
+
+
+def test_batched_plan_auto_path_is_fastest_tensor_path():
+    if not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    host, dev = make_batch(SMALL[:2], 47)
+    plan = bmm.BatchedPlan([s[3] for s in SMALL[:2]], [d[0] for d in dev], [d[1] for d in dev],
+                           [d[2] for d in dev], [s[0] for s in SMALL[:2]],
+                           [s[1] for s in SMALL[:2]], [s[2] for s in SMALL[:2]])
+    assert plan.path() == bmm.plan(bmm.GF2, 4096, 4096, 4096, depth=0)["path"]
+    assert plan.path() == bmm.PATH_TC_FP4_PAIR
+    plan.destroy()
+
+
 def test_uniform_op_batched_entry_points():
     shapes = [(s[0], s[1], s[2], 0) for s in SMALL[:4]]
     host, dev = make_batch(shapes, 42)

@@ -102,7 +102,8 @@ def test_config2_square32768_bench_launch_configuration():
 
 def test_config3_square65536_paths_agree():
     """m = k = n = 65536, seed 3: the tensor-core base cases (one SM or an SM
-    pair per tile) and the CUDA-core base case give bit-identical products
+    pair per tile, e4m3 or e2m1 operands) and the CUDA-core base case give
+    bit-identical products
     (cubic), and match the oracle's samples; the planner's Strassen product
     matches too. GF(2) p = 1/2, Boolean p = 2^-8."""
     n, seed = 65536, 3
@@ -115,6 +116,9 @@ def test_config3_square65536_paths_agree():
         tp = run_product(op, n, seed, ids, p, path=bmm.PATH_TC_FP8_PAIR, depth=0)
         assert (tp == tc).all(), f"SM-pair vs single-SM tensor paths disagree (op={op})"
         del tp
+        t4 = run_product(op, n, seed, ids, p, path=bmm.PATH_TC_FP4_PAIR, depth=0)
+        assert (t4 == tc).all(), f"e2m1 vs e4m3 tensor paths disagree (op={op})"
+        del t4
         if op == bmm.GF2:
             st = run_product(op, n, seed, ids, p)
             assert (st == tc).all(), "Strassen (planner rule) vs cubic disagree"

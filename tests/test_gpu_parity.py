@@ -23,7 +23,7 @@ OPS = {bmm.GF2: O.GF2, bmm.BOOL: O.BOOL}
 def paths():
     ps = [bmm.PATH_POPC]
     if bmm.device_supported():
-        ps += [bmm.PATH_TC_FP8, bmm.PATH_TC_FP8_PAIR]
+        ps += list(bmm.TENSOR_PATHS)
     return ps
 
 
@@ -120,13 +120,16 @@ def prefix_rows(counts, k):
 @pytest.mark.parametrize("path", paths())
 def test_base_product_exact_counts_past_2pow23(path):
     """Prefix rows: entry (i, j) of the integer product is min(c_i, d_j), a closed
-    form. k = 2^23 + 2^21 bits takes the counts past 2^23, where the fp8 path
-    must flush its FP32 accumulator (it reads parity off count * 2^-12, exact
-    below 2^23), and puts every parity next to 2^22, 2^23 and k."""
+    form. k = 2^23 + 2^21 bits takes the counts past 2^23, where the tensor
+    paths must flush their FP32 accumulator (they read parity off
+    count * 2^-12, exact below 2^23: every 65534 stages of 128 k for e4m3,
+    32766 of 256 k for e2m1), and puts every parity next to 2^22, 2^23, both
+    flush points and k."""
     m, n, k = 128, 256, (1 << 23) + (1 << 21)
     rng = np.random.default_rng(31)
     edge = [0, 1, 2, 63, 64, 65, (1 << 22) - 1, 1 << 22, (1 << 22) + 1,
-            65534 * 128 - 1, 65534 * 128, 65534 * 128 + 1, (1 << 23) - 1, 1 << 23,
+            65534 * 128 - 1, 65534 * 128, 65534 * 128 + 1, 32766 * 256 - 1, 32766 * 256,
+            32766 * 256 + 1, (1 << 23) - 1, 1 << 23,
             (1 << 23) + 1, k - 1, k]
     c = edge + rng.integers(0, k + 1, m - len(edge)).tolist()
     d = [k] * (n // 2) + edge + rng.integers(0, k + 1, n // 2 - len(edge)).tolist()
@@ -166,13 +169,13 @@ def test_tensor_paths_pad_k(m, k, n, depth):
         p = None if op == bmm.GF2 else "1/16"
         Ah, Bh = gen(m, k, 37, 0, p), gen(k, n, 37, 1, p)
         want = O.cubic(OPS[op], Ah, Bh, m, k, n)
-        for path in (bmm.PATH_TC_FP8, bmm.PATH_TC_FP8_PAIR):
+        for path in bmm.TENSOR_PATHS:
             info = bmm.plan(op, m, k, n, path=path, depth=depth)
             assert info["path"] == path
             check(run(op, Ah, Bh, m, k, n, path=path, depth=depth), want,
                   f"padded k op={op} path={path} depth={depth}")
         if depth == 0:  # the automatic choice takes a tensor path too
-            assert bmm.plan(op, m, k, n)["path"] in (bmm.PATH_TC_FP8, bmm.PATH_TC_FP8_PAIR)
+            assert bmm.plan(op, m, k, n)["path"] in bmm.TENSOR_PATHS
             check(run(op, Ah, Bh, m, k, n), want, f"padded k auto op={op}")
 
 

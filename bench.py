@@ -53,8 +53,9 @@ FP4_PER_BF16 = 6.0
 # FP8 MACs per clock per SM of tcgen05.mma kind::f8f6f4 on sm_103 (measured
 # with back-to-back MMAs); 2 FLOP each.
 FP8_MAC_PER_SM_CLK = 8192
-# FP4 (kind::mxf4) MACs per clock per SM: the nominal FP4 : FP8 ratio (3 : 1).
-FP4_MAC_PER_SM_CLK = 24576
+# FP4 MACs per clock per SM of tcgen05.mma kind::mxf4 (block scale every 32 k)
+# on sm_103 (measured with back-to-back MMAs: twice the FP8 rate).
+FP4_MAC_PER_SM_CLK = 16384
 
 # DRAM bytes (read + write) of the base-case launches of one step of the
 # default workload, from one ncu capture (dram__bytes_read.sum +
@@ -63,9 +64,9 @@ FP4_MAC_PER_SM_CLK = 24576
 # (GF(2) depth 3 with one depth-first level: 7 leaf launches + 1 Boolean).
 TRAFFIC_RECORD = {
     "kernel": "paper_1909_01554_gb300/csrc/tc_gemm.cu",
-    "sha256": "7a0832a3a419c81fe92e1311f1e87b455972dcdf9b09dc0b22a42cab5ea8deab",
+    "sha256": "f0dedd3d55465d55fb3389374e1fb2d896168c9fdcb871048733ac75e46ef753",
     "workload": "square32768", "gf2_depth": 3, "gf2_serial": 1, "base_launches": 8,
-    "dram_bytes_per_step": 2780954112,
+    "dram_bytes_per_step": 2781093120,
 }
 
 
@@ -197,34 +198,64 @@ def max_over_ranks(x: float, dist) -> float:
 
 def pipelined(torch, stream, steps: int, upload, compute, download) -> float:
     """Runs `steps` end-to-end steps over two device buffer sets and returns the
-    milliseconds from the first upload to the last read-back. upload(j) and
-    download(j) run on a copy stream, compute(j) on `stream`; set j is
-    re-uploaded only after its compute (and the read-back before it) is done."""
-    cs = torch.cuda.Stream()
-    ready = [torch.cuda.Event() for _ in range(2)]
-    done = [torch.cuda.Event() for _ in range(2)]
+    milliseconds from the first upload to the last read-back. upload(j) runs on
+    an upload stream, download(j) on a read-back stream (the two directions of
+    the host link overlap) and compute(j) on `stream`. Set j is re-uploaded
+    once its compute has read it, and computed into again only after its
+    previous products have been read back."""
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    ready = [torch.cuda.Event() for _ in range(2)]     # inputs of set j uploaded
+    done = [torch.cuda.Event() for _ in range(2)]      # compute on set j finished
+    fetched = [torch.cuda.Event() for _ in range(2)]   # products of set j read back
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    cs.wait_event(e0)
-    with torch.cuda.stream(cs):
+    up.wait_event(e0)
+    down.wait_event(e0)
+    with torch.cuda.stream(up):
         for j in range(min(2, steps)):
             upload(j)
-            ready[j].record(cs)
+            ready[j].record(up)
     for i in range(steps):
         j = i % 2
         stream.wait_event(ready[j])
+        if i >= 2:
+            stream.wait_event(fetched[j])
         with torch.cuda.stream(stream):
             compute(j)
         done[j].record(stream)
-        cs.wait_event(done[j])
-        with torch.cuda.stream(cs):
+        down.wait_event(done[j])
+        with torch.cuda.stream(down):
             download(j)
-            if i + 2 < steps:
+        fetched[j].record(down)
+        if i + 2 < steps:
+            up.wait_event(done[j])
+            with torch.cuda.stream(up):
                 upload(j)
-                ready[j].record(cs)
-    e1.record(cs)
+            ready[j].record(up)
+    stream.wait_event(fetched[(steps - 1) % 2])
+    e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1)
+
+
+OVERLAP = ("double-buffered: uploads and read-backs on two copy streams (both directions of "
+           "the host link at once) while the other buffer set computes")
+
+
+def copy_times(torch, upload, download) -> dict:
+    """Milliseconds of one step's upload and one read-back alone (after a
+    warm-up), to set beside the end-to-end time."""
+    out = {}
+    for name, fn in (("h2d_ms", upload), ("d2h_ms", download)):
+        fn(0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn(0)
+        b.record()
+        torch.cuda.synchronize()
+        out[name] = a.elapsed_time(b)
+    return out
 
 
 def job_rate(world: int, units_per_step: float, steps: int, ms: float) -> float:
@@ -488,8 +519,8 @@ def main():
         ems = max_over_ranks(ems, dist)
         e2e = {"value": job_rate(world, bops_step, args.steps, ems), "unit": "bop/s",
                "h2d_bytes_per_step": 4 * m * k // 8, "d2h_bytes_per_step": 2 * m * n // 8,
-               "overlap": "double-buffered: upload of step i+1 and read-back of step i on a "
-                          "copy stream while step i+1 computes"}
+               "ms_per_step": ems / args.steps, **copy_times(torch, upload, download),
+               "overlap": OVERLAP}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -714,11 +745,11 @@ def run_batched(args):
         torch.cuda.synchronize()
         ems = max_over_ranks(pipelined(torch, stream, args.steps, upload, compute, download),
                              dist)
+        copies = copy_times(torch, upload, download)
         plan2.destroy()
         e2e = {"value": job_rate(world, bops_step, args.steps, ems), "unit": "bop/s",
                "h2d_bytes_per_step": d_in.numel() * 8, "d2h_bytes_per_step": d_out.numel() * 8,
-               "overlap": "double-buffered: upload of step i+1 and read-back of step i on a "
-                          "copy stream while step i+1 computes"}
+               "ms_per_step": ems / args.steps, **copies, "overlap": OVERLAP}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -190,6 +190,59 @@ bmm_status bmm_batched_plan_destroy(bmm_batched_plan plan);
 /* The base-case path (bmm_path, never AUTO) the plan runs. */
 bmm_status bmm_batched_plan_path(bmm_batched_plan plan, int32_t *path);
 
+/* ---- operands in host memory: the host layer (Secs. 3.12-3.14, Alg. 3) ---
+ *
+ * C = A B with A, B and C in host memory (same packed row-major layout as on
+ * the device), for products whose operands need not fit the device. Binary
+ * product: the host expands `host_depth` Strassen levels into 7^host_depth
+ * sub-instances (each block combination of A and B that the combined masks
+ * of those levels select, Eq. igen), the device solves each with its own
+ * plan, and the host adds every solution into the C blocks it belongs to
+ * (Eq. iagg); host threads generate and aggregate while the device computes
+ * and the host link copies, all double-buffered. Boolean product (no
+ * additive inverse), or host_depth 0: C is computed in blocks that fit the
+ * device, streaming row panels of A and column panels of B from the
+ * caller's arrays and C blocks back into C.
+ *
+ * Pinned host memory (cudaHostAlloc / cudaHostRegister) lets the copies run
+ * asynchronously; pageable memory works with staged copies. The calls block
+ * until C is complete in host memory; `stream` carries the device work.
+ * Errors: as bmm_gf2 (sizes, alignment, overlap of C with A or B);
+ * BMM_ERR_NOMEM if no blocking fits `device_bytes` or host staging cannot
+ * be pinned; host_depth > 0 for the Boolean product is BMM_ERR_INVALID; a
+ * host_depth whose 64 * 2^host_depth does not divide m, k and n is
+ * BMM_ERR_UNSUPPORTED. */
+typedef struct {
+    bmm_opts device;        /* options of each product on the device (path, Strassen
+                               depth, variant; also the host levels' variant);
+                               the workspace fields are ignored */
+    uint64_t device_bytes;  /* device memory the call may use; 0: 80 % of free memory */
+    int32_t host_depth;     /* binary product: Strassen levels on the host; -1: none
+                               if the whole product fits, else the fewest that make a
+                               sub-instance fit, else blocks of C; 0: never */
+    int32_t threads;        /* host threads for generation and aggregation; 0: all */
+} bmm_host_opts;
+
+void bmm_host_opts_default(bmm_host_opts *opts);
+
+/* What a host-memory product with these arguments does (no device needed
+ * when opts->device_bytes is non-zero). */
+typedef struct {
+    int32_t host_depth;             /* Strassen levels run on the host */
+    int64_t sub_m, sub_k, sub_n;    /* shape of one device product */
+    int64_t count;                  /* device products */
+    uint64_t device_bytes;          /* device memory the call needs (estimate) */
+    uint64_t staging_bytes;         /* pinned host staging it allocates */
+    uint64_t upload_bytes, download_bytes;  /* host <-> device traffic */
+} bmm_host_plan_info;
+
+bmm_status bmm_host_plan(int32_t op, int64_t m, int64_t k, int64_t n, const bmm_host_opts *opts,
+                         bmm_host_plan_info *info);
+bmm_status bmm_gf2_host(const uint64_t *A, const uint64_t *B, uint64_t *C, int64_t m, int64_t k,
+                        int64_t n, const bmm_host_opts *opts, bmm_stream_t stream);
+bmm_status bmm_bool_host(const uint64_t *A, const uint64_t *B, uint64_t *C, int64_t m, int64_t k,
+                         int64_t n, const bmm_host_opts *opts, bmm_stream_t stream);
+
 /* ---- the steps of the path, exported for tests and experiments ---------- */
 
 /* Bit transpose: Xt (cols x rows) = X^T (X is rows x cols). The paper

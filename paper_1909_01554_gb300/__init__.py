@@ -30,6 +30,7 @@ EXPORTED = [
     "bmm_device_supported", "bmm_plan", "bmm_product_noalloc", "bmm_selftest_wait_timeout",
     "bmm_trace_enable", "bmm_trace_read", "bmm_launch_count", "bmm_autotune",
     "bmm_autotune_clear", "bmm_batched_plan_path", "bmm_batched_plan_create_ex",
+    "bmm_host_opts_default", "bmm_host_plan", "bmm_gf2_host", "bmm_bool_host",
 ]
 TUNE_MODEL = 1
 PHASE_BASE, PHASE_XOR, PHASE_TRANSPOSE = 0, 1, 2
@@ -54,6 +55,18 @@ class Opts(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("best", Opts), ("est_ms", ctypes.c_double), ("measured", ctypes.c_int32),
                 ("candidates", ctypes.c_int32)]
+
+
+class HostOpts(ctypes.Structure):
+    _fields_ = [("device", Opts), ("device_bytes", ctypes.c_uint64),
+                ("host_depth", ctypes.c_int32), ("threads", ctypes.c_int32)]
+
+
+class HostPlanInfo(ctypes.Structure):
+    _fields_ = [("host_depth", ctypes.c_int32), ("sub_m", ctypes.c_int64),
+                ("sub_k", ctypes.c_int64), ("sub_n", ctypes.c_int64), ("count", ctypes.c_int64),
+                ("device_bytes", ctypes.c_uint64), ("staging_bytes", ctypes.c_uint64),
+                ("upload_bytes", ctypes.c_uint64), ("download_bytes", ctypes.c_uint64)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -129,6 +142,14 @@ def _lib_handle():
         L.bmm_autotune.restype = i32
         L.bmm_autotune_clear.argtypes = []
         L.bmm_autotune_clear.restype = None
+        L.bmm_host_opts_default.argtypes = [ctypes.POINTER(HostOpts)]
+        L.bmm_host_opts_default.restype = None
+        L.bmm_host_plan.argtypes = [i32, i64, i64, i64, ctypes.POINTER(HostOpts),
+                                    ctypes.POINTER(HostPlanInfo)]
+        L.bmm_host_plan.restype = i32
+        for f in (L.bmm_gf2_host, L.bmm_bool_host):
+            f.argtypes = [vp, vp, vp, i64, i64, i64, ctypes.POINTER(HostOpts), vp]
+            f.restype = i32
         _LIB = L
     return _LIB
 
@@ -151,7 +172,11 @@ def _stream(stream):
 def _ptr(t) -> int:
     if t is None:
         return 0
-    return t if isinstance(t, int) else t.data_ptr()
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data  # numpy array in host memory
 
 
 def _check(status: int, what: str):
@@ -245,6 +270,39 @@ def plan(op: int, m: int, k: int, n: int, **kw) -> dict:
     info = PlanInfo()
     _check(_lib_handle().bmm_plan(op, m, k, n, ctypes.byref(o), ctypes.byref(info)), "bmm_plan")
     return {f: int(getattr(info, f)) for f, _ in PlanInfo._fields_}
+
+
+def host_opts(device_bytes: int = 0, host_depth: int = -1, threads: int = 0,
+              **kw) -> HostOpts:
+    """Options of a host-memory product (bmm_host_opts); kw as opts() for the
+    device products."""
+    o = HostOpts()
+    _lib_handle().bmm_host_opts_default(ctypes.byref(o))
+    o.device = opts(**kw)
+    o.device_bytes = device_bytes
+    o.host_depth = host_depth
+    o.threads = threads
+    return o
+
+
+def host_plan(op: int, m: int, k: int, n: int, **kw) -> dict:
+    """What a host-memory product with these sizes does (host levels, device
+    products, memory and traffic)."""
+    o = host_opts(**kw)
+    info = HostPlanInfo()
+    _check(_lib_handle().bmm_host_plan(op, m, k, n, ctypes.byref(o), ctypes.byref(info)),
+           "bmm_host_plan")
+    return {f: int(getattr(info, f)) for f, _ in HostPlanInfo._fields_}
+
+
+def product_host(op: int, A, B, C, m: int, k: int, n: int, stream=None, **kw) -> None:
+    """C = A B with A, B, C in host memory (numpy arrays or CPU tensors, packed
+    row-major words; pinned memory overlaps the copies). Blocks until C is
+    complete."""
+    o = host_opts(**kw)
+    f = _lib_handle().bmm_gf2_host if op == GF2 else _lib_handle().bmm_bool_host
+    _check(f(_ptr(A), _ptr(B), _ptr(C), m, k, n, ctypes.byref(o), _stream(stream)),
+           "bmm_gf2_host" if op == GF2 else "bmm_bool_host")
 
 
 def transpose(X, Xt, rows: int, cols: int, stream=None) -> None:

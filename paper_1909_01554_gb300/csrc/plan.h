@@ -24,6 +24,10 @@ struct Plan {
 
 bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* opts, Plan* out);
 
+// Scratch bytes of a plan with these sizes, Strassen depth and depth-first
+// levels, k padded to kp (a padded copy of A when kp != k).
+uint64_t workspace_padded(int64_t m, int64_t k, int64_t kp, int64_t n, int depth, int serial);
+
 // Bytes the plan's streaming passes move through HBM: the transpose of B and
 // every XOR pass (depth-first combine / fold, breadth-first expand /
 // compress), not counting the base case.

@@ -112,3 +112,31 @@ def test_batched_plan_argument_checks_need_no_gpu(built_lib):
     assert h.value is None
     p = ctypes.c_int32(0)
     assert L.bmm_batched_plan_path(None, ctypes.byref(p)) == bmm.ERR_INVALID
+
+
+def test_host_product_argument_checks_need_no_gpu(built_lib):
+    """Host-memory products reject bad sizes, null, misaligned and overlapping
+    arrays, host Strassen levels for the Boolean product and bad options
+    before any CUDA call."""
+    import ctypes
+
+    import numpy as np
+
+    import paper_1909_01554_gb300 as bmm
+
+    L = bmm.lib()
+    A = np.zeros(64 * 64 // 64 + 2, dtype=np.uint64)
+    a = A.ctypes.data
+    o = bmm.host_opts(device_bytes=1 << 30)
+    ob = bmm.host_opts(device_bytes=1 << 30, host_depth=1)
+    for f in (L.bmm_gf2_host, L.bmm_bool_host):
+        assert f(a, a, 0, 64, 64, 64, ctypes.byref(o), None) == bmm.ERR_INVALID
+        assert f(a, a, a + 4096, 96, 64, 64, ctypes.byref(o), None) == bmm.ERR_INVALID
+        assert f(a + 8, a, a + 4096, 64, 64, 64, ctypes.byref(o), None) == bmm.ERR_ALIGN
+        assert f(a, a, a, 64, 64, 64, ctypes.byref(o), None) == bmm.ERR_INVALID  # C overlaps A
+    assert L.bmm_bool_host(a, a, a + 4096, 64, 64, 64, ctypes.byref(ob), None) == bmm.ERR_INVALID
+    bad = bmm.host_opts(device_bytes=1 << 30, host_depth=-2)
+    assert L.bmm_gf2_host(a, a, a + 4096, 64, 64, 64, ctypes.byref(bad), None) == bmm.ERR_INVALID
+    info = bmm.HostPlanInfo()
+    assert L.bmm_host_plan(2, 64, 64, 64, ctypes.byref(o), ctypes.byref(info)) == bmm.ERR_INVALID
+    assert L.bmm_host_plan(0, 64, 64, 64, ctypes.byref(o), None) == bmm.ERR_INVALID

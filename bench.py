@@ -38,7 +38,11 @@ WORKLOADS = {
     # 2048 problems, m, k, n log-uniform in [256, 8192] (multiples of 64), 50/50
     # GF(2) (p = 1/2) / Boolean (p = 1/sqrt(k)); problem i uses seed 5 * 2^16 + i
     "batched2048": (2048, 5, "1/sqrt(k)"),
+    # operands and products in pinned host memory, through the host layer with
+    # a device budget below the product's in-HBM footprint (out of core)
+    "host65536": (65536, 3, "2^-8"),
 }
+HOST_DEVICE_BYTES = {"host65536": 3 << 30}
 DEFAULT_WORKLOAD = "square32768"
 # Matrix ids of the generator streams: GF(2) pair (0, 1), Boolean pair (4, 5).
 IDS_GF2 = (0, 1)
@@ -362,6 +366,8 @@ def main():
         return run_reference(args)
     if args.workload.startswith("batched"):
         return run_batched(args)
+    if args.workload.startswith("host"):
+        return run_host(args)
 
     import torch
 
@@ -593,6 +599,134 @@ def oracle_batched_sample(probs, target_s: float):
         if tot_s >= target_s:
             break
     return tot_s, bops, used, th
+
+
+def run_host(args):
+    """Host-memory products (the host layer): A, B and C in pinned host memory,
+    the device limited to HOST_DEVICE_BYTES; a step is one GF(2) and one
+    Boolean product, each a blocking library call from host arrays to host
+    arrays (so every step moves its inputs in and its products out)."""
+    import torch
+
+    import bitgen
+    import paper_1909_01554_gb300 as bmm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n, seed, bool_p = WORKLOADS[args.workload]
+    m = k = n
+    budget = HOST_DEVICE_BYTES[args.workload]
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    def gen(rows, cols, mid, p):
+        t = bmm.empty(rows, cols)
+        bitgen.fill_device(t, cols, seed, mid, p=p, stream=sh)
+        h = t.cpu().pin_memory()
+        del t
+        return h
+
+    Ag, Bg = gen(m, k, IDS_GF2[0], None), gen(k, n, IDS_GF2[1], None)
+    Ab, Bb = gen(m, k, IDS_BOOL[0], bool_p), gen(k, n, IDS_BOOL[1], bool_p)
+    Cg = torch.empty(m * n // 64, dtype=torch.int64).pin_memory()
+    Cb = torch.empty(m * n // 64, dtype=torch.int64).pin_memory()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    kw = {"device_bytes": budget}
+    pg = bmm.host_plan(bmm.GF2, m, k, n, **kw)
+    pb = bmm.host_plan(bmm.BOOL, m, k, n, **kw)
+
+    def step(mid=None):
+        bmm.product_host(bmm.GF2, Ag, Bg, Cg, m, k, n, stream=sh, **kw)
+        if mid is not None:
+            mid.record(stream)
+        bmm.product_host(bmm.BOOL, Ab, Bb, Cb, m, k, n, stream=sh, **kw)
+
+    for _ in range(args.warmup):
+        step()
+    bmm.stream_status(sh)
+    sampler = ClockSampler(torch.cuda.current_device())
+    bmm.trace_enable(True)
+    l0 = bmm.launch_count()
+    sampler.start()
+    time.sleep(0.3)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    torch.cuda.synchronize()
+    marks[0].record(stream)
+    for i in range(args.steps):
+        step(mid=marks[2 * i + 1])
+        marks[2 * i + 2].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = bmm.launch_count() - l0
+    bmm.trace_enable(False)
+    bmm.stream_status(sh)
+    ms = max_over_ranks(marks[0].elapsed_time(marks[-1]), dist)
+    per_product = {
+        "gf2": sum(marks[2 * i].elapsed_time(marks[2 * i + 1]) for i in range(args.steps))
+        / args.steps,
+        "bool": sum(marks[2 * i + 1].elapsed_time(marks[2 * i + 2]) for i in range(args.steps))
+        / args.steps,
+    }
+    base_n, base_ms = bmm.trace_read(bmm.PHASE_BASE)
+    bops_step = 2 * (2 * m * k * n)
+    value = job_rate(world, bops_step, args.steps, ms)
+    # base-case work: every device product's leaves (GF(2)) or its cubic work
+    sg = bmm.plan(bmm.GF2, pg["sub_m"], pg["sub_k"], pg["sub_n"])
+    d = sg["strassen_depth"]
+    flops = (2 * pg["count"] * sg["leaves"] * (pg["sub_m"] >> d) * (pg["sub_k"] >> d)
+             * (pg["sub_n"] >> d) + 2 * m * k * n)
+    pk, pk_kind = peaks()
+    fp4 = sg["path"] == bmm.PATH_TC_FP4_PAIR
+    peak, peak_source = tensor_peak(pk, pk_kind, fp4)
+    achieved = flops * args.steps / (base_ms / 1000.0) / 1e12 if base_ms > 0 else 0.0
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": peak_source,
+            **tensor_pipe(achieved, clocks, pk["sm_max_mhz"], fp4)}
+    h2d = pg["upload_bytes"] + pb["upload_bytes"]
+    d2h = pg["download_bytes"] + pb["download_bytes"]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(n, seed, bool_p)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "bop/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "e2m1" if fp4 else "e4m3",
+            "data": "synthetic (seeded SplitMix64 Bernoulli bits), pinned host memory",
+            "config": {"workload": args.workload, "m": m, "k": k, "n": n,
+                       "device_bytes": budget,
+                       "gf2": f"p=1/2, {pg['host_depth']} host Strassen levels: "
+                              f"{pg['count']} device products of {pg['sub_m']}^3 "
+                              f"(device Strassen depth {d})",
+                       "bool": f"p={bool_p}, C in {pb['count']} blocks of "
+                               f"{pb['sub_m']} x {pb['sub_n']}",
+                       "l2": "inputs larger than L2 (each operand "
+                             f"{m * k // 8 // 2**20} MiB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "bop/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "note": "the step itself runs host arrays to host arrays"},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "product_ms": per_product,
+            "product_bops": {op: 2 * m * k * n / (t / 1000.0) for op, t in per_product.items()},
+            "host_plans": {"gf2": pg, "bool": pb},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
 
 
 def run_batched(args):

@@ -236,12 +236,14 @@ void generate(const uint64_t* X, int64_t rows, int64_t words, int d, const uint3
     });
 }
 
-// Q_h into every C block whose zeta product is 1 (Eq. iagg); a block's first
-// contribution is copied, later ones are added.
+// Q_h into every C block whose zeta product is 1 (Eq. iagg), in one pass
+// over Q's rows; a block's first contribution is copied, later ones added.
 void aggregate(uint64_t* C, int64_t rows, int64_t words, int d, const uint32_t* zeta,
                const int* dig, const std::vector<BlockRef>& refs, std::vector<char>& seen,
                const uint64_t* Q, int threads) {
     const int64_t sr = rows >> d, sw = words >> d;
+    std::vector<BlockRef> dst;
+    std::vector<char> first;
     for (size_t t = 0; t < refs.size(); t++) {
         bool on = true;
         int64_t x = (int64_t)t;
@@ -251,20 +253,22 @@ void aggregate(uint64_t* C, int64_t rows, int64_t words, int d, const uint32_t* 
             on = (zeta[q] >> dig[l]) & 1u;
         }
         if (!on) continue;
-        const bool first = !seen[t];
+        dst.push_back(refs[t]);
+        first.push_back(!seen[t]);
         seen[t] = 1;
-        const BlockRef b = refs[t];
-        parallel_rows(sr, threads, [&](int64_t r0, int64_t r1) {
-            for (int64_t i = r0; i < r1; i++) {
-                uint64_t* dst = C + (b.row + i) * words + b.word;
-                const uint64_t* q = Q + i * sw;
-                if (first)
-                    std::memcpy(dst, q, (size_t)sw * 8);
-                else
-                    for (int64_t w = 0; w < sw; w++) dst[w] ^= q[w];
-            }
-        });
     }
+    parallel_rows(sr, threads, [&](int64_t r0, int64_t r1) {
+        for (int64_t i = r0; i < r1; i++) {
+            const uint64_t* q = Q + i * sw;
+            for (size_t j = 0; j < dst.size(); j++) {
+                uint64_t* c = C + (dst[j].row + i) * words + dst[j].word;
+                if (first[j])
+                    std::memcpy(c, q, (size_t)sw * 8);
+                else
+                    for (int64_t w = 0; w < sw; w++) c[w] ^= q[w];
+            }
+        }
+    });
 }
 
 // ---------------------------------------------------------------- device side
@@ -475,8 +479,10 @@ bmm_status run_host_strassen(const HostPlan& hp, const bmm_host_opts& ho, const 
     cudaEvent_t* down_done = sx.ev + 4;  // [2] Q of the slot downloaded
     int dev = 0;
     cudaGetDevice(&dev);
+    // generation and aggregation of neighbouring sub-instances overlap in
+    // time, and each is memory-bound: both get every thread
     const int threads = host_threads(ho);
-    const int gen_threads = std::max(1, threads / 2), agg_threads = std::max(1, threads - gen_threads);
+    const int gen_threads = threads, agg_threads = threads;
     const std::vector<BlockRef> refA = block_refs(d, m, k / 64);
     const std::vector<BlockRef> refB = block_refs(d, k, n / 64);
     const std::vector<BlockRef> refC = block_refs(d, m, n / 64);

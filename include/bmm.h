@@ -240,6 +240,10 @@ bmm_status bmm_host_plan(int32_t op, int64_t m, int64_t k, int64_t n, const bmm_
                          bmm_host_plan_info *info);
 bmm_status bmm_gf2_host(const uint64_t *A, const uint64_t *B, uint64_t *C, int64_t m, int64_t k,
                         int64_t n, const bmm_host_opts *opts, bmm_stream_t stream);
+/* The host-memory products keep their pinned staging and device buffers
+ * between calls on a device (allocating them is a large share of one call);
+ * calls on one device are serialised. This frees them on every device. */
+void bmm_host_release(void);
 bmm_status bmm_bool_host(const uint64_t *A, const uint64_t *B, uint64_t *C, int64_t m, int64_t k,
                          int64_t n, const bmm_host_opts *opts, bmm_stream_t stream);
 

@@ -31,6 +31,7 @@ EXPORTED = [
     "bmm_trace_enable", "bmm_trace_read", "bmm_launch_count", "bmm_autotune",
     "bmm_autotune_clear", "bmm_batched_plan_path", "bmm_batched_plan_create_ex",
     "bmm_host_opts_default", "bmm_host_plan", "bmm_gf2_host", "bmm_bool_host",
+    "bmm_host_release",
 ]
 TUNE_MODEL = 1
 PHASE_BASE, PHASE_XOR, PHASE_TRANSPOSE = 0, 1, 2
@@ -150,6 +151,8 @@ def _lib_handle():
         for f in (L.bmm_gf2_host, L.bmm_bool_host):
             f.argtypes = [vp, vp, vp, i64, i64, i64, ctypes.POINTER(HostOpts), vp]
             f.restype = i32
+        L.bmm_host_release.argtypes = []
+        L.bmm_host_release.restype = None
         _LIB = L
     return _LIB
 
@@ -303,6 +306,11 @@ def product_host(op: int, A, B, C, m: int, k: int, n: int, stream=None, **kw) ->
     f = _lib_handle().bmm_gf2_host if op == GF2 else _lib_handle().bmm_bool_host
     _check(f(_ptr(A), _ptr(B), _ptr(C), m, k, n, ctypes.byref(o), _stream(stream)),
            "bmm_gf2_host" if op == GF2 else "bmm_bool_host")
+
+
+def host_release() -> None:
+    """Free the buffers host-memory products keep between calls."""
+    _lib_handle().bmm_host_release()
 
 
 def transpose(X, Xt, rows: int, cols: int, stream=None) -> None:

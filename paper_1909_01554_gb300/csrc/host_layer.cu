@@ -272,41 +272,62 @@ void aggregate(uint64_t* C, int64_t rows, int64_t words, int d, const uint32_t* 
 }
 
 // ---------------------------------------------------------------- device side
-struct DevBuf {
+// Buffers kept between host-memory products on a device: pinning hundreds
+// of MB of staging and allocating GBs of device memory cost tens of ms, a
+// large share of one product. A call holds its device's cache (mutex),
+// grows what it needs and leaves it for the next call;
+// bmm_host_release frees it.
+struct Cached {
     void* p = nullptr;
-    ~DevBuf() {
-        if (p) cudaFree(p);
-    }
-    bmm_status get(uint64_t bytes) {
-        if (bytes == 0) return BMM_OK;
-        const cudaError_t e = cudaMalloc(&p, bytes);
+    uint64_t bytes = 0;
+    bool pinned = false;
+    bmm_status want(uint64_t b) {
+        if (b <= bytes) return BMM_OK;
+        release();
+        const cudaError_t e = pinned ? cudaHostAlloc(&p, b, cudaHostAllocDefault) : cudaMalloc(&p, b);
         if (e != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
             return cuda_fail(e);
         }
+        bytes = b;
         return BMM_OK;
+    }
+    void release() {
+        if (p) {
+            if (pinned)
+                cudaFreeHost(p);
+            else
+                cudaFree(p);
+        }
+        p = nullptr;
+        bytes = 0;
     }
     uint64_t* w() const { return (uint64_t*)p; }
 };
 
-struct HostBuf {
-    void* p = nullptr;
-    ~HostBuf() {
-        if (p) cudaFreeHost(p);
+struct HostCache {
+    std::mutex mu;
+    // device: [0, 2) left operand slots, [2, 4) right, [4, 6) product, 6 scratch
+    Cached dev[7];
+    // pinned staging: [0, 2) T, [2, 4) S, [4, 6) Q
+    Cached host[6];
+    HostCache() {
+        for (auto& h : host) h.pinned = true;
     }
-    bmm_status get(uint64_t bytes) {
-        if (bytes == 0) return BMM_OK;
-        const cudaError_t e = cudaHostAlloc(&p, bytes, cudaHostAllocDefault);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-            return cuda_fail(e);
-        }
-        return BMM_OK;
+    uint64_t device_bytes() const {
+        uint64_t b = 0;
+        for (const auto& d : dev) b += d.bytes;
+        return b;
     }
-    uint64_t* w() const { return (uint64_t*)p; }
+    void release() {
+        for (auto& d : dev) d.release();
+        for (auto& h : host) h.release();
+    }
 };
+
+constexpr int MAX_DEVICES = 64;
+HostCache g_cache[MAX_DEVICES];
 
 struct Streams {
     cudaStream_t up = nullptr, down = nullptr;
@@ -346,18 +367,21 @@ struct PlanCache {
 
 // Blocks of C, each with full k, streamed from and to the caller's arrays.
 bmm_status run_blocked(const HostPlan& hp, const bmm_host_opts& ho, const uint64_t* A,
-                       const uint64_t* B, uint64_t* C, cudaStream_t comp) {
+                       const uint64_t* B, uint64_t* C, cudaStream_t comp, HostCache& hc) {
     const int64_t m = hp.m, k = hp.k, n = hp.n, bm = hp.bm, bn = hp.bn;
     const int64_t kw = k / 64, nw = n / 64;
     const int64_t rm = (m + bm - 1) / bm, rn = (n + bn - 1) / bn;
     PlanCache pc{hp.op, ho.device, {}};
     pc.o.workspace = nullptr;
     pc.o.workspace_bytes = 0;
-    DevBuf dA[2], dB[2], dC[2], ws;
+    Cached* dA = hc.dev;
+    Cached* dB = hc.dev + 2;
+    Cached* dC = hc.dev + 4;
+    Cached& ws = hc.dev[6];
     for (int i = 0; i < 2; i++) {
-        bmm_status st = dA[i].get((uint64_t)bm * k / 8);
-        if (st == BMM_OK) st = dB[i].get((uint64_t)k * bn / 8);
-        if (st == BMM_OK) st = dC[i].get((uint64_t)bm * bn / 8);
+        bmm_status st = dA[i].want((uint64_t)bm * k / 8);
+        if (st == BMM_OK) st = dB[i].want((uint64_t)k * bn / 8);
+        if (st == BMM_OK) st = dC[i].want((uint64_t)bm * bn / 8);
         if (st != BMM_OK) return st;
     }
     uint64_t wsb = 0;
@@ -368,7 +392,7 @@ bmm_status run_blocked(const HostPlan& hp, const bmm_host_opts& ho, const uint64
             if (st != BMM_OK) return st;
             wsb = std::max(wsb, pl->workspace_bytes);
         }
-    bmm_status st = ws.get(wsb);
+    bmm_status st = ws.want(wsb);
     if (st != BMM_OK) return st;
     Streams sx;
     if ((st = sx.make()) != BMM_OK) return st;
@@ -442,7 +466,7 @@ struct Slots {
 };
 
 bmm_status run_host_strassen(const HostPlan& hp, const bmm_host_opts& ho, const uint64_t* A,
-                             const uint64_t* B, uint64_t* C, cudaStream_t comp) {
+                             const uint64_t* B, uint64_t* C, cudaStream_t comp, HostCache& hc) {
     const int d = hp.host_depth;
     const int64_t m = hp.m, k = hp.k, n = hp.n;
     const int64_t sm = m >> d, sk = k >> d, sn = n >> d;
@@ -457,21 +481,26 @@ bmm_status run_host_strassen(const HostPlan& hp, const bmm_host_opts& ho, const 
     PlanCache pc{hp.op, ho.device, {}};
     pc.o.workspace = nullptr;
     pc.o.workspace_bytes = 0;
-    DevBuf dT[2], dS[2], dQ[2], ws;
-    HostBuf hT[2], hS[2], hQ[2];
+    Cached* dT = hc.dev;
+    Cached* dS = hc.dev + 2;
+    Cached* dQ = hc.dev + 4;
+    Cached& ws = hc.dev[6];
+    Cached* hT = hc.host;
+    Cached* hS = hc.host + 2;
+    Cached* hQ = hc.host + 4;
     bmm_status st = BMM_OK;
     for (int i = 0; i < 2 && st == BMM_OK; i++) {
-        st = dT[i].get(tb);
-        if (st == BMM_OK) st = dS[i].get(sb);
-        if (st == BMM_OK) st = dQ[i].get(qb);
-        if (st == BMM_OK) st = hT[i].get(tb);
-        if (st == BMM_OK) st = hS[i].get(sb);
-        if (st == BMM_OK) st = hQ[i].get(qb);
+        st = dT[i].want(tb);
+        if (st == BMM_OK) st = dS[i].want(sb);
+        if (st == BMM_OK) st = dQ[i].want(qb);
+        if (st == BMM_OK) st = hT[i].want(tb);
+        if (st == BMM_OK) st = hS[i].want(sb);
+        if (st == BMM_OK) st = hQ[i].want(qb);
     }
     if (st != BMM_OK) return st;
     const Plan* pl = nullptr;
     if ((st = pc.get(sm, sk, sn, &pl)) != BMM_OK) return st;
-    if ((st = ws.get(pl->workspace_bytes)) != BMM_OK) return st;
+    if ((st = ws.want(pl->workspace_bytes)) != BMM_OK) return st;
     Streams sx;
     if ((st = sx.make()) != BMM_OK) return st;
     cudaEvent_t* up_done = sx.ev;    // [2] T/S of the slot uploaded (staging free)
@@ -584,6 +613,7 @@ bmm_status check_host_args(int op, const uint64_t* A, const uint64_t* B, const u
     if (op != OP_GF2 && op != OP_BOOL) return BMM_ERR_INVALID;
     if (m <= 0 || k <= 0 || n <= 0 || m % 64 || k % 64 || n % 64) return BMM_ERR_INVALID;
     if (opts && (opts->host_depth < -1 || opts->threads < 0)) return BMM_ERR_INVALID;
+    if (opts && opts->host_depth > 0 && op != OP_GF2) return BMM_ERR_INVALID;  // no additive inverse
     if (!A || !B || !C) return BMM_ERR_INVALID;
     if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)C) & 15u) return BMM_ERR_ALIGN;
     const uint64_t ab = (uint64_t)m * k / 8, bb = (uint64_t)k * n / 8, cb = (uint64_t)m * n / 8;
@@ -595,15 +625,22 @@ bmm_status check_host_args(int op, const uint64_t* A, const uint64_t* B, const u
     return BMM_OK;
 }
 
-bmm_status budget_of(const bmm_host_opts& ho, uint64_t* budget) {
+// cached: device bytes this device's cache already holds (usable again)
+bmm_status budget_of(const bmm_host_opts& ho, uint64_t cached, uint64_t* budget) {
     if (ho.device_bytes) {
         *budget = ho.device_bytes;
         return BMM_OK;
     }
     size_t fr = 0, tot = 0;
     BMM_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-    *budget = (uint64_t)(fr * 0.8);
+    *budget = (uint64_t)((fr + cached) * 0.8);
     return BMM_OK;
+}
+
+HostCache* device_cache() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= MAX_DEVICES) return nullptr;
+    return &g_cache[d];
 }
 
 bmm_status host_product(int op, const uint64_t* A, const uint64_t* B, uint64_t* C, int64_t m,
@@ -613,12 +650,18 @@ bmm_status host_product(int op, const uint64_t* A, const uint64_t* B, uint64_t* 
     bmm_host_opts ho;
     bmm_host_opts_default(&ho);
     if (opts) ho = *opts;
+    HostCache* hc = device_cache();
+    if (!hc) return BMM_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(hc->mu);
     uint64_t budget = 0;
-    if ((st = budget_of(ho, &budget)) != BMM_OK) return st;
+    if ((st = budget_of(ho, hc->device_bytes(), &budget)) != BMM_OK) return st;
     HostPlan hp;
     if ((st = host_plan(op, m, k, n, ho, budget, &hp)) != BMM_OK) return st;
-    return hp.host_depth > 0 ? run_host_strassen(hp, ho, A, B, C, s)
-                             : run_blocked(hp, ho, A, B, C, s);
+    // a larger plan than the cache holds: release first, so that the old and
+    // the new buffers never coexist against the budget
+    if (hc->device_bytes() > 0 && hp.device_bytes > hc->device_bytes()) hc->release();
+    return hp.host_depth > 0 ? run_host_strassen(hp, ho, A, B, C, s, *hc)
+                             : run_blocked(hp, ho, A, B, C, s, *hc);
 }
 
 }  // namespace
@@ -646,7 +689,7 @@ bmm_status bmm_host_plan(int32_t op, int64_t m, int64_t k, int64_t n, const bmm_
     bmm_host_opts_default(&ho);
     if (opts) ho = *opts;
     uint64_t budget = 0;
-    bmm_status st = budget_of(ho, &budget);
+    bmm_status st = budget_of(ho, 0, &budget);
     if (st != BMM_OK) return st;
     HostPlan hp;
     if ((st = host_plan(op, m, k, n, ho, budget, &hp)) != BMM_OK) return st;
@@ -660,6 +703,18 @@ bmm_status bmm_host_plan(int32_t op, int64_t m, int64_t k, int64_t n, const bmm_
     info->upload_bytes = hp.upload_bytes;
     info->download_bytes = hp.download_bytes;
     return BMM_OK;
+}
+
+void bmm_host_release(void) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (int d = 0; d < MAX_DEVICES; d++) {
+        std::lock_guard<std::mutex> lk(g_cache[d].mu);
+        if (g_cache[d].device_bytes() == 0 && !g_cache[d].host[0].p) continue;
+        cudaSetDevice(d);
+        g_cache[d].release();
+    }
+    cudaSetDevice(cur);
 }
 
 bmm_status bmm_gf2_host(const uint64_t* A, const uint64_t* B, uint64_t* C, int64_t m, int64_t k,

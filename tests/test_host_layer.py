@@ -167,3 +167,20 @@ def test_gf2_host_levels_over_device_strassen():
     got = host_product(bmm.GF2, Ah, Bh, n, n, n, pinned=True, host_depth=2, depth=2,
                        device_bytes=1 << 30)
     assert (got == O.cubic(O.GF2, Ah, Bh, n, n, n)).all()
+
+
+@pytest.mark.gpu
+def test_cached_buffers_across_calls_and_release():
+    """Consecutive host-memory products reuse (and grow) the kept buffers:
+    small, large, small again, then after a release; every result exact."""
+    if not gpu_ok():
+        pytest.skip("no GPU")
+    cases = [(512, 1024, 512, 1), (1024, 2048, 1536, 1), (512, 1024, 512, 1), (768, 640, 960, 0)]
+    for i, (m, k, n, hd) in enumerate(cases):
+        if i == 3:
+            bmm.host_release()
+        op = bmm.GF2
+        Ah, Bh = gen(m, k, 79 + i, 0), gen(k, n, 79 + i, 1)
+        got = host_product(op, Ah, Bh, m, k, n, pinned=True, host_depth=hd, device_bytes=1 << 30)
+        assert (got == O.cubic(O.GF2, Ah, Bh, m, k, n)).all(), (m, k, n, hd)
+    bmm.host_release()

@@ -831,7 +831,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             // moves by EB_BYTES >> 4 per stage; every stage lies below 256 KB,
             // so no carry
             const uint64_t db_base = smem_desc_sw128(sbase + LY::OFF_EB);
+            // The issuing thread's own instructions sit on the tensor pipe's
+            // critical path (one extra branch per stage measured 5 %), so the
+            // slot and its phase are running counters, not divisions.
+            static_assert(LY::WAITG == 1 || LY::WAITG == 2, "wait groups of one or two slots");
             int seg = 0, pit = 0;
+            int q = 0;         // pit % OSLOTS
+            uint32_t ph = 0;   // (pit / OSLOTS) & 1
             bool ok = true;
             for (int i = 0; ok && i < my_tiles; i++) {
                 const int nks = tile_nks<BATCHED, PAIR>(p, i);
@@ -841,11 +847,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                     // the last of WAITG consecutive slots covers them all. At a
                     // tile's first stage the operands are checked before the
                     // (longer) wait for the epilogue to free the accumulator.
-                    const bool group = pit % LY::WAITG == 0;
+                    const bool group = (pit & (LY::WAITG - 1)) == 0;
                     if (group) {
-                        const int w = pit + LY::WAITG - 1 < total_pit ? pit + LY::WAITG - 1
-                                                                      : total_pit - 1;
-                        if (!mbar_wait(full_o(w % OSLOTS), (w / OSLOTS) & 1, p.err)) {
+                        int qw = q;
+                        uint32_t phw = ph;
+                        if (LY::WAITG == 2 && pit + 1 < total_pit && ++qw == OSLOTS) {
+                            qw = 0;
+                            phw ^= 1u;
+                        }
+                        if (!mbar_wait(full_o(qw), phw, p.err)) {
                             ok = false;
                             break;
                         }
@@ -857,7 +867,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                         }
                     }
                     if (group || kin == 0) tc_fence_after();
-                    const int q = pit % OSLOTS;
 #pragma unroll
                     for (int sub = 0; sub < SUB; sub++) {
                         const int e = 2 * q + sub;
@@ -876,6 +885,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                         }
                     }
                     mma_commit<PAIR>(empty_o(q));
+                    if (++q == OSLOTS) {
+                        q = 0;
+                        ph ^= 1u;
+                    }
                     kin += SUB;
                     if (kin >= kchunk || ks + SUB >= nks) {
                         mma_commit<PAIR>(acc_full);

@@ -68,9 +68,9 @@ FP4_MAC_PER_SM_CLK = 16384
 # (GF(2) depth 3 with one depth-first level: 7 leaf launches + 1 Boolean).
 TRAFFIC_RECORD = {
     "kernel": "paper_1909_01554_gb300/csrc/tc_gemm.cu",
-    "sha256": "f0dedd3d55465d55fb3389374e1fb2d896168c9fdcb871048733ac75e46ef753",
+    "sha256": "5c57557433ed3bf31eaf70e005186cb49c2d5c1dfde93e17c9f8296d1a72288e",
     "workload": "square32768", "gf2_depth": 3, "gf2_serial": 1, "base_launches": 8,
-    "dram_bytes_per_step": 2781093120,
+    "dram_bytes_per_step": 2782182912,
 }
 
 

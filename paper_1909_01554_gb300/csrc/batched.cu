@@ -117,22 +117,28 @@ bmm_status plan_build(bmm_batched_plan_s* P, int path) {
             pads++;
         }
     }
-    // tiles and their LPT assignment
+    // tiles and their LPT assignment (cost: k stages plus an epilogue share)
     std::vector<TcWorkItem> items;
+    std::vector<int32_t> cost_of(count);
     for (int i = 0; i < count; i++) {
         const int tm_n = (int)((P->m[i] + tile_m - 1) / tile_m);
         const int tn_n = (int)((P->n[i] + TC_TILE_N - 1) / TC_TILE_N);
         // cost: k in 128-bit units (the e2m1 form's stages carry twice the k
         // for about the same time, as far as the tensor rate allows)
         const int kstage = P->fp4 ? 512 : 256;
-        const int nks = (int)((P->k[i] + kstage - 1) / kstage) * 2;
+        // the padded k the problem's maps are built with (tc_make_problem)
+        const int64_t kpad = P->kp[i] * 64;
+        const int nks = (int)((kpad + kstage - 1) / kstage) * 2;
         for (int a = 0; a < tm_n; a++)
-            for (int b = 0; b < tn_n; b++) items.push_back({i, a, b, nks + EPI_COST});
+            for (int b = 0; b < tn_n; b++) items.push_back({i, a, b, nks});
+        cost_of[i] = nks + EPI_COST;
     }
     const int slots = P->pair ? pair_slots : sm_count();
     const int grid = (int)std::min<int64_t>((int64_t)items.size(), slots);  // work units
     std::stable_sort(items.begin(), items.end(),
-                     [](const TcWorkItem& x, const TcWorkItem& y) { return x.cost > y.cost; });
+                     [&](const TcWorkItem& x, const TcWorkItem& y) {
+                         return cost_of[x.prob] > cost_of[y.prob];
+                     });
     std::vector<std::vector<TcWorkItem>> per(grid);
     using Load = std::pair<int64_t, int>;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
@@ -141,15 +147,22 @@ bmm_status plan_build(bmm_batched_plan_s* P, int path) {
         Load l = heap.top();
         heap.pop();
         per[l.second].push_back(w);
-        l.first += w.cost;
+        l.first += cost_of[w.prob];
         heap.push(l);
     }
-    std::vector<int32_t> cta_ptr(grid + 1, 0);
+    // item offsets per unit, then each unit's packed stages (the kernel's
+    // roles size their loops by it without walking the list)
+    std::vector<int32_t> cta_ptr(2 * (grid + 1), 0);
     std::vector<TcWorkItem> flat;
     flat.reserve(items.size());
     for (int c = 0; c < grid; c++) {
         cta_ptr[c] = (int32_t)flat.size();
-        for (const TcWorkItem& w : per[c]) flat.push_back(w);
+        int64_t pits = 0;
+        for (const TcWorkItem& w : per[c]) {
+            flat.push_back(w);
+            pits += (w.nks + 1) / 2;
+        }
+        cta_ptr[grid + 1 + c] = (int32_t)pits;
     }
     cta_ptr[grid] = (int32_t)flat.size();
     P->grid = grid;
@@ -158,7 +171,7 @@ bmm_status plan_build(bmm_batched_plan_s* P, int path) {
     const uint64_t off_probs = round256(ws);
     const uint64_t off_items = round256(off_probs + sizeof(TcProblem) * (uint64_t)count);
     const uint64_t off_ptr = round256(off_items + sizeof(TcWorkItem) * flat.size());
-    const uint64_t off_tjobs = round256(off_ptr + sizeof(int32_t) * (grid + 1));
+    const uint64_t off_tjobs = round256(off_ptr + sizeof(int32_t) * 2 * (grid + 1));
     const uint64_t off_tfirst = round256(off_tjobs + sizeof(TransposeJob) * (uint64_t)count);
     const uint64_t off_pjobs = round256(off_tfirst + sizeof(int64_t) * (uint64_t)(count + 1));
     const uint64_t off_pfirst = round256(off_pjobs + sizeof(PadJob) * (uint64_t)std::max(pads, 1));
@@ -210,7 +223,7 @@ bmm_status plan_build(bmm_batched_plan_s* P, int path) {
     if (!flat.empty())
         BMM_CUDA_TRY(cudaMemcpy(P->d_items, flat.data(), sizeof(TcWorkItem) * flat.size(),
                                 cudaMemcpyHostToDevice));
-    BMM_CUDA_TRY(cudaMemcpy(P->d_cta_ptr, cta_ptr.data(), sizeof(int32_t) * (grid + 1),
+    BMM_CUDA_TRY(cudaMemcpy(P->d_cta_ptr, cta_ptr.data(), sizeof(int32_t) * 2 * (grid + 1),
                             cudaMemcpyHostToDevice));
     BMM_CUDA_TRY(cudaMemcpy(P->d_tjobs, tjobs.data(), sizeof(TransposeJob) * count,
                             cudaMemcpyHostToDevice));

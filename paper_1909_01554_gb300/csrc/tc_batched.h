@@ -22,7 +22,7 @@ struct TcProblem {
 // One output tile (TC_TILE_M rows, or 2 * TC_TILE_M for an SM pair, x
 // TC_TILE_N columns) of one problem; tm counts tiles of that height.
 struct TcWorkItem {
-    int32_t prob, tm, tn, cost;
+    int32_t prob, tm, tn, nks;  // nks: the problem's k stages (read without the problem table)
 };
 
 constexpr int TC_TILE_M = 128;
@@ -38,8 +38,10 @@ bool tc_make_problem(TcProblem* out, const uint64_t* A, int64_t lda, const uint6
                      int64_t ldb, uint64_t* C, int64_t ldc, int64_t m, int64_t k, int64_t n,
                      int op, bool pair, bool fp4);
 
-// One persistent launch over the per-unit work lists (unit_ptr has units + 1
-// entries); a unit is one CTA, or one CTA pair when `pair`.
+// One persistent launch over the per-unit work lists; a unit is one CTA, or
+// one CTA pair when `pair`. unit_ptr has 2 * (units + 1) entries: the first
+// units + 1 delimit each unit's items, entry units + 1 + u is unit u's
+// number of packed stages (two k stages each, the last one possibly half).
 cudaError_t tc_launch_batched(const TcProblem* d_probs, const TcWorkItem* d_items,
                               const int32_t* d_unit_ptr, int units, bool pair, bool fp4,
                               cudaStream_t s);

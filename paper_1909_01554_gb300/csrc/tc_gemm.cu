@@ -595,7 +595,7 @@ __device__ __forceinline__ Tile tile_get(const Params& p, int idx, const CUtenso
 
 template <bool BATCHED, bool PAIR>
 __device__ __forceinline__ int tile_nks(const Params& p, int idx) {
-    if (BATCHED) return p.probs[p.items[p.cta_ptr[unit_id<PAIR>()] + idx].prob].nks;
+    if (BATCHED) return p.items[p.cta_ptr[unit_id<PAIR>()] + idx].nks;
     return p.nks;
 }
 
@@ -661,8 +661,11 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     const int kchunk = p.kchunk;
     const int my_tiles = tile_count<BATCHED, PAIR>(p);
-    int total_pit = 0;  // packed stages this CTA runs
-    for (int i = 0; i < my_tiles; i++) total_pit += tile_nks<BATCHED, PAIR>(p, i) / SUB;
+    int total_pit = 0;  // packed stages this CTA runs (batched: from the plan)
+    if (BATCHED)
+        total_pit = p.cta_ptr[unit_count<PAIR>() + 1 + unit_id<PAIR>()];
+    else
+        total_pit = my_tiles * (p.nks / SUB);
 
     if (warp == TMA_WARP) {
         // ---------------------------------------------------- TMA producer
@@ -839,8 +842,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             int q = 0;         // pit % OSLOTS
             uint32_t ph = 0;   // (pit / OSLOTS) & 1
             bool ok = true;
+            // a tile's k stages are loaded one tile ahead (batched: from the
+            // work list in global memory, off the issue path)
+            int nks_next = my_tiles > 0 ? tile_nks<BATCHED, PAIR>(p, 0) : 0;
             for (int i = 0; ok && i < my_tiles; i++) {
-                const int nks = tile_nks<BATCHED, PAIR>(p, i);
+                const int nks = nks_next;
+                if (i + 1 < my_tiles) nks_next = tile_nks<BATCHED, PAIR>(p, i + 1);
                 int kin = 0;
                 for (int ks = 0; ks < nks; ks += SUB, pit++) {
                     // Every producer fills the slots in order, so one wait on

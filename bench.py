@@ -68,9 +68,9 @@ FP4_MAC_PER_SM_CLK = 16384
 # (GF(2) depth 3 with one depth-first level: 7 leaf launches + 1 Boolean).
 TRAFFIC_RECORD = {
     "kernel": "paper_1909_01554_gb300/csrc/tc_gemm.cu",
-    "sha256": "5c57557433ed3bf31eaf70e005186cb49c2d5c1dfde93e17c9f8296d1a72288e",
+    "sha256": "810229f441732f46e02577ed858e817c8ac75f65962c9664880c002a8add0680",
     "workload": "square32768", "gf2_depth": 3, "gf2_serial": 1, "base_launches": 8,
-    "dram_bytes_per_step": 2782182912,
+    "dram_bytes_per_step": 2782602752,
 }
 
 

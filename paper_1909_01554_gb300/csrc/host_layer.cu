@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <condition_variable>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -156,22 +157,80 @@ int host_threads(const bmm_host_opts& ho) {
     return h > 0 ? (int)h : 1;
 }
 
-// f(r0, r1) over row ranges, on up to `threads` threads.
+// Persistent workers for one host role's passes (a pass runs part i of n on
+// worker i, the calling thread being worker 0, and returns when all parts
+// are done): threads are started once per product, not once per pass.
+class Pool {
+  public:
+    explicit Pool(int n) : size_(std::max(1, n)) {
+        for (int i = 1; i < size_; i++) th_.emplace_back([this, i]() { worker(i); });
+    }
+    ~Pool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto& t : th_) t.join();
+    }
+    int size() const { return size_; }
+    // f(i) for i in [0, parts), parts <= size()
+    void run(int parts, const std::function<void(int)>& f) {
+        if (parts <= 1 || th_.empty()) {
+            for (int i = 0; i < parts; i++) f(i);
+            return;
+        }
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            job_ = &f;
+            parts_ = parts;
+            remaining_ = (int)th_.size();
+            gen_++;
+        }
+        cv_.notify_all();
+        f(0);
+        std::unique_lock<std::mutex> lk(mu_);
+        done_.wait(lk, [&]() { return remaining_ == 0; });
+        job_ = nullptr;
+    }
+
+  private:
+    void worker(int id) {
+        uint64_t seen = 0;
+        for (;;) {
+            const std::function<void(int)>* j = nullptr;
+            int parts = 0;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&]() { return stop_ || gen_ != seen; });
+                if (stop_) return;
+                seen = gen_;
+                j = job_;
+                parts = parts_;
+            }
+            if (id < parts) (*j)(id);
+            {
+                std::lock_guard<std::mutex> lk(mu_);
+                if (--remaining_ == 0) done_.notify_all();
+            }
+        }
+    }
+    int size_;
+    std::vector<std::thread> th_;
+    std::mutex mu_;
+    std::condition_variable cv_, done_;
+    const std::function<void(int)>* job_ = nullptr;
+    int parts_ = 0, remaining_ = 0;
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+
+// f(r0, r1) over row ranges, on the pool's workers.
 template <class F>
-void parallel_rows(int64_t rows, int threads, F f) {
+void parallel_rows(int64_t rows, Pool& pool, F f) {
     const int64_t per_min = 16;
-    const int p = (int)std::max<int64_t>(1, std::min<int64_t>(threads, rows / per_min));
-    if (p == 1) {
-        f((int64_t)0, rows);
-        return;
-    }
-    std::vector<std::thread> th;
-    th.reserve(p);
-    for (int i = 0; i < p; i++) {
-        const int64_t r0 = rows * i / p, r1 = rows * (i + 1) / p;
-        th.emplace_back([=]() { f(r0, r1); });
-    }
-    for (auto& t : th) t.join();
+    const int p = (int)std::max<int64_t>(1, std::min<int64_t>(pool.size(), rows / per_min));
+    pool.run(p, [&](int i) { f(rows * i / p, rows * (i + 1) / p); });
 }
 
 // Block of a matrix at nested quadrant indices (q_1 .. q_d), outer level
@@ -210,7 +269,7 @@ void digits7(int64_t h, int d, int* dig) {
 // Tuples whose product of level masks is 1: sum of X blocks into out
 // (Eq. igen, one sub-instance).
 void generate(const uint64_t* X, int64_t rows, int64_t words, int d, const uint32_t* mask,
-              const int* dig, const std::vector<BlockRef>& refs, uint64_t* out, int threads) {
+              const int* dig, const std::vector<BlockRef>& refs, uint64_t* out, Pool& pool) {
     std::vector<BlockRef> src;
     for (size_t t = 0; t < refs.size(); t++) {
         bool on = true;
@@ -223,7 +282,7 @@ void generate(const uint64_t* X, int64_t rows, int64_t words, int d, const uint3
         if (on) src.push_back(refs[t]);
     }
     const int64_t sr = rows >> d, sw = words >> d;
-    parallel_rows(sr, threads, [&](int64_t r0, int64_t r1) {
+    parallel_rows(sr, pool, [&](int64_t r0, int64_t r1) {
         for (int64_t i = r0; i < r1; i++) {
             uint64_t* dst = out + i * sw;
             const uint64_t* s0 = X + (src[0].row + i) * words + src[0].word;
@@ -240,7 +299,7 @@ void generate(const uint64_t* X, int64_t rows, int64_t words, int d, const uint3
 // over Q's rows; a block's first contribution is copied, later ones added.
 void aggregate(uint64_t* C, int64_t rows, int64_t words, int d, const uint32_t* zeta,
                const int* dig, const std::vector<BlockRef>& refs, std::vector<char>& seen,
-               const uint64_t* Q, int threads) {
+               const uint64_t* Q, Pool& pool) {
     const int64_t sr = rows >> d, sw = words >> d;
     std::vector<BlockRef> dst;
     std::vector<char> first;
@@ -257,7 +316,7 @@ void aggregate(uint64_t* C, int64_t rows, int64_t words, int d, const uint32_t* 
         first.push_back(!seen[t]);
         seen[t] = 1;
     }
-    parallel_rows(sr, threads, [&](int64_t r0, int64_t r1) {
+    parallel_rows(sr, pool, [&](int64_t r0, int64_t r1) {
         for (int64_t i = r0; i < r1; i++) {
             const uint64_t* q = Q + i * sw;
             for (size_t j = 0; j < dst.size(); j++) {
@@ -521,6 +580,7 @@ bmm_status run_host_strassen(const HostPlan& hp, const bmm_host_opts& ho, const 
 
     std::thread generator([&]() {
         cudaSetDevice(dev);
+        Pool pool(gen_threads);
         for (int64_t h = 0; h < count; h++) {
             const int g = (int)(h & 1);
             // the slot's previous sub-instance must have left for the device
@@ -532,13 +592,14 @@ bmm_status run_host_strassen(const HostPlan& hp, const bmm_host_opts& ho, const 
             }
             int dig[8];
             digits7(h, d, dig);
-            generate(A, m, k / 64, d, xi, dig, refA, hT[g].w(), gen_threads);
-            generate(B, k, n / 64, d, eta, dig, refB, hS[g].w(), gen_threads);
+            generate(A, m, k / 64, d, xi, dig, refA, hT[g].w(), pool);
+            generate(B, k, n / 64, d, eta, dig, refB, hS[g].w(), pool);
             sl.update([&]() { sl.generated[g] = h; });
         }
     });
     std::thread aggregator([&]() {
         cudaSetDevice(dev);
+        Pool pool(agg_threads);
         for (int64_t h = 0; h < count; h++) {
             const int g = (int)(h & 1);
             if (!sl.wait([&]() { return sl.downloaded[g] >= h; })) return;
@@ -549,7 +610,7 @@ bmm_status run_host_strassen(const HostPlan& hp, const bmm_host_opts& ho, const 
             }
             int dig[8];
             digits7(h, d, dig);
-            aggregate(C, m, n / 64, d, zeta, dig, refC, seen, hQ[g].w(), agg_threads);
+            aggregate(C, m, n / 64, d, zeta, dig, refC, seen, hQ[g].w(), pool);
             sl.update([&]() { sl.aggregated[g] = h; });
         }
     });

@@ -48,7 +48,8 @@ DEFAULT_WORKLOAD = "square32768"
 IDS_GF2 = (0, 1)
 IDS_BOOL = (4, 5)
 
-# 32-bit LOP3 results per SM per clock on sm_103 (measured).
+# 32-bit LOP3 results per SM per clock on sm_103 (measured with a
+# dependent-chain microbenchmark; IMAD also 64, POPC 16).
 LOP3_LANES_PER_SM_CLK = 64
 # Nominal dense FP8 : BF16 tensor throughput ratio (4.5 : 2.25 PFLOP/s).
 FP8_PER_BF16 = 2.0

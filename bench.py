@@ -126,6 +126,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="planner rules instead of the autotuner")
+    ap.add_argument("--kernel-level", type=int, default=0, choices=[0, 1],
+                    help="GF(2): run the innermost Strassen level inside the base-case kernel "
+                         "(CUDA-core path)")
     return ap.parse_args()
 
 
@@ -407,6 +410,8 @@ def main():
     Ab, Bb = gen(m, k, IDS_BOOL[0], bool_p), gen(k, n, IDS_BOOL[1], bool_p)
     Cg, Cb = bmm.empty(m, n), bmm.empty(m, n)
     kw_g = {"path": path, "depth": args.depth}
+    if args.kernel_level:
+        kw_g["kernel_level"] = args.kernel_level
     kw_b = {"path": path}
     # The autotuner picks base-case path and Strassen depth by measurement
     # (outside the timed region) wherever both are left to the library.
@@ -541,7 +546,9 @@ def main():
             "data": "synthetic (seeded SplitMix64 Bernoulli bits)",
             "config": {"workload": args.workload, "m": m, "k": k, "n": n,
                        "gf2": f"p=1/2, Strassen depth {depth_g} ({leaves} leaves), "
-                              f"self-inverse alternative basis",
+                              f"self-inverse alternative basis"
+                              + (", innermost level inside the base-case kernel"
+                                 if pg["kernel_level"] else ""),
                        "bool": f"p={bool_p}, cubic", "base_case": _path_name(resolved),
                        "bool_base_case": _path_name(pb["path"]),
                        "l2": f"inputs larger than L2 (each operand {m * k // 8 // 2**20} MiB)",

@@ -82,6 +82,14 @@ typedef struct {
     int32_t serial_depth;    /* -1 auto; top levels run depth-first (Sec. 3.8) */
     void *workspace;         /* optional device scratch; NULL: stream-ordered allocation */
     uint64_t workspace_bytes;
+    int32_t kernel_level;    /* 1: the innermost Strassen level runs inside the base-case
+                                kernel, which forms each of the 7 products' operands from
+                                the quadrants as it stages them and folds the products
+                                into the C quadrants in registers (no leaf operands or
+                                leaf products in HBM). Binary product on the CUDA-core
+                                path only (BMM_PATH_POPC, or AUTO where it resolves
+                                there), else BMM_ERR_UNSUPPORTED; a plan without Strassen
+                                levels ignores it. 0 (default): every level in XOR passes */
 } bmm_opts;
 
 /* Fills opts with the defaults (auto path, auto depth, self-inverse variant). */
@@ -116,6 +124,7 @@ typedef struct {
     int32_t variant;
     int64_t leaves;
     uint64_t workspace_bytes;
+    int32_t kernel_level;    /* 1: the innermost of the levels runs inside the base case */
 } bmm_plan_info;
 bmm_status bmm_plan(int32_t op, int64_t m, int64_t k, int64_t n, const bmm_opts *opts,
                     bmm_plan_info *info);

@@ -50,7 +50,8 @@ class BmmError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("strassen_depth", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("serial_depth", ctypes.c_int32),
-                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64)]
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
+                ("kernel_level", ctypes.c_int32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -73,7 +74,8 @@ class HostPlanInfo(ctypes.Structure):
 class PlanInfo(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("strassen_depth", ctypes.c_int32),
                 ("serial_depth", ctypes.c_int32), ("variant", ctypes.c_int32),
-                ("leaves", ctypes.c_int64), ("workspace_bytes", ctypes.c_uint64)]
+                ("leaves", ctypes.c_int64), ("workspace_bytes", ctypes.c_uint64),
+                ("kernel_level", ctypes.c_int32)]
 
 
 _LIB = None
@@ -188,7 +190,8 @@ def _check(status: int, what: str):
 
 
 def opts(path: int | None = None, depth: int | None = None, variant: int | None = None,
-         serial: int | None = None, workspace=None, workspace_bytes: int = 0) -> Opts:
+         serial: int | None = None, workspace=None, workspace_bytes: int = 0,
+         kernel_level: int | None = None) -> Opts:
     o = Opts()
     _lib_handle().bmm_opts_default(ctypes.byref(o))
     if path is not None:
@@ -199,6 +202,8 @@ def opts(path: int | None = None, depth: int | None = None, variant: int | None 
         o.variant = variant
     if serial is not None:
         o.serial_depth = serial
+    if kernel_level is not None:
+        o.kernel_level = kernel_level
     if workspace is not None:
         o.workspace = _ptr(workspace)
         o.workspace_bytes = workspace_bytes

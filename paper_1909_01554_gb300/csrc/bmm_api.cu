@@ -199,6 +199,7 @@ bmm_status bmm_plan(int32_t op, int64_t m, int64_t k, int64_t n, const bmm_opts*
     for (int i = 0; i < p.depth; i++) leaves *= 7;
     info->leaves = leaves;
     info->workspace_bytes = p.workspace_bytes;
+    info->kernel_level = p.kernel_level;
     return BMM_OK;
 }
 

@@ -80,4 +80,20 @@ cudaError_t launch_popc_nt(int op, const uint64_t* A, int64_t lda, int64_t strid
                            int64_t ldc, int64_t strideC, int64_t count, int64_t m, int64_t k,
                            int64_t n, cudaStream_t s);
 
+// Combined standard-basis operators of one Strassen level as 0/1 masks:
+// xi[h] bit q = block q of A enters product h, eta[h] likewise for B,
+// zeta[q] bit h = product h enters block q of C (blocks q = 2*row + col).
+struct LevelMasks {
+    uint32_t xi[7], eta[7], zeta[4];
+};
+
+// The binary product of each block of a batch through one Strassen level run
+// inside the CUDA-core kernel: C (m x n) = A (m x k) Bt^T (Bt n x k), the
+// seven quadrant products formed, multiplied and recombined in one launch
+// (strides and pitches as launch_popc_nt). m even; k and n multiples of 128.
+cudaError_t launch_popc_level(const uint64_t* A, int64_t lda, int64_t strideA, const uint64_t* Bt,
+                              int64_t ldb, int64_t strideB, uint64_t* C, int64_t ldc,
+                              int64_t strideC, int64_t count, int64_t m, int64_t k, int64_t n,
+                              const LevelMasks& masks, cudaStream_t s);
+
 }  // namespace bmm

@@ -73,6 +73,7 @@ uint64_t workspace_for(int64_t m, int64_t k, int64_t n, int depth, int serial) {
 
 struct Exec {
     const Plan& p;
+    const int od;  // levels outside the base case (the last one may run inside it)
     char* ws;
     cudaStream_t s;
     uint32_t xi[7], eta[7], zeta[4];
@@ -83,7 +84,8 @@ struct Exec {
     uint64_t* R[8] = {nullptr};
     uint64_t *TL = nullptr, *SL = nullptr, *QL = nullptr;
 
-    Exec(const Plan& plan, void* w, cudaStream_t st) : p(plan), ws((char*)w), s(st) {
+    Exec(const Plan& plan, void* w, cudaStream_t st)
+        : p(plan), od(plan.depth - plan.kernel_level), ws((char*)w), s(st) {
         switch (p.variant) {
             case 0: slp::level_masks<0>(xi, eta, zeta); break;
             case 1: slp::level_masks<1>(xi, eta, zeta); break;
@@ -97,19 +99,38 @@ struct Exec {
         };
         Bt = take((uint64_t)p.kp * p.n / 8);
         if (p.kp != p.k) Apad = take((uint64_t)p.m * p.kp / 8);
-        const int bufs = fused_last_serial(p.depth, p.serial) ? p.serial - 1 : p.serial;
+        const int bufs = fused_last_serial(od, p.serial) ? p.serial - 1 : p.serial;
         for (int l = 1; l <= bufs; l++) {
             T[l] = take((uint64_t)(p.m >> l) * (p.kp >> l) / 8);
             S[l] = take((uint64_t)(p.n >> l) * (p.kp >> l) / 8);
             R[l] = take((uint64_t)(p.m >> l) * (p.n >> l) / 8);
         }
-        const int dp = p.depth - p.serial;
+        const int dp = od - p.serial;
         if (dp > 0) {
             const uint64_t r = (uint64_t)ipow7(dp);
-            TL = take(r * (uint64_t)(p.m >> p.depth) * (p.kp >> p.depth) / 8);
-            SL = take(r * (uint64_t)(p.n >> p.depth) * (p.kp >> p.depth) / 8);
-            QL = take(r * (uint64_t)(p.m >> p.depth) * (p.n >> p.depth) / 8);
+            TL = take(r * (uint64_t)(p.m >> od) * (p.kp >> od) / 8);
+            SL = take(r * (uint64_t)(p.n >> od) * (p.kp >> od) / 8);
+            QL = take(r * (uint64_t)(p.m >> od) * (p.n >> od) / 8);
         }
+    }
+
+    // The product of `count` blocks below the outer levels (strides in words):
+    // the base case, or the innermost Strassen level with the base case
+    // inside one kernel.
+    bmm_status blocks(const uint64_t* A, int64_t lda, int64_t sa, const uint64_t* B, int64_t ldb,
+                      int64_t sb, uint64_t* C, int64_t ldc, int64_t sc, int64_t count, int64_t m,
+                      int64_t k, int64_t n) {
+        if (p.kernel_level) {
+            LevelMasks lm;
+            std::memcpy(lm.xi, xi, sizeof xi);
+            std::memcpy(lm.eta, eta, sizeof eta);
+            std::memcpy(lm.zeta, zeta, sizeof zeta);
+            BMM_CUDA_TRY(launch_popc_level(A, lda, sa, B, ldb, sb, C, ldc, sc, count, m, k, n, lm,
+                                           s));
+            return BMM_OK;
+        }
+        return run_base_product_batched(p.op, p.path, A, lda, sa, B, ldb, sb, C, ldc, sc, count,
+                                        m, k, n, s);
     }
 
     bmm_status level(int l, const uint64_t* A, int64_t lda, const uint64_t* B, int64_t ldb,
@@ -117,7 +138,7 @@ struct Exec {
         if (l < p.serial) {
             const int64_t hm = m / 2, hk = k / 2, hn = n / 2;
             uint32_t first = 0xF;
-            if (l + 1 == p.serial && fused_last_serial(p.depth, p.serial)) {
+            if (l + 1 == p.serial && fused_last_serial(od, p.serial)) {
                 for (int h = 0; h < 7; h++) {
                     uint32_t dest = 0;
                     for (int q = 0; q < 4; q++) dest |= ((zeta[q] >> h) & 1u) << q;
@@ -144,8 +165,7 @@ struct Exec {
             }
             return BMM_OK;
         }
-        if (p.depth == l)
-            return run_base_product(p.op, p.path, A, lda, B, ldb, C, ldc, m, k, n, s);
+        if (od == l) return blocks(A, lda, 0, B, ldb, 0, C, ldc, 0, 1, m, k, n);
         return leaves(A, lda, 0, B, ldb, 0, C, ldc, 0, 0, m, k, n);
     }
 
@@ -157,14 +177,13 @@ struct Exec {
     bmm_status leaves(const uint64_t* A, int64_t lda, uint32_t amask, const uint64_t* B,
                       int64_t ldb, uint32_t bmask, uint64_t* C, int64_t ldc, uint32_t dest,
                       uint32_t first, int64_t m, int64_t k, int64_t n) {
-        const int dp = p.depth - p.serial;
+        const int dp = od - p.serial;
         const int64_t lm = m >> dp, lk = k >> dp, ln = n >> dp;
         BMM_CUDA_TRY(launch_expand(p.variant, 0, dp, A, lda, m, k / 64, amask, TL, s));
         BMM_CUDA_TRY(launch_expand(p.variant, 1, dp, B, ldb, n, k / 64, bmask, SL, s));
         const int64_t count = ipow7(dp);
-        bmm_status st = run_base_product_batched(p.op, p.path, TL, lk / 64, lm * lk / 64, SL,
-                                                 lk / 64, ln * lk / 64, QL, ln / 64, lm * ln / 64,
-                                                 count, lm, lk, ln, s);
+        bmm_status st = blocks(TL, lk / 64, lm * lk / 64, SL, lk / 64, ln * lk / 64, QL, ln / 64,
+                               lm * ln / 64, count, lm, lk, ln);
         if (st != BMM_OK) return st;
         BMM_CUDA_TRY(launch_compress(p.variant, dp, QL, lm, ln / 64, C, ldc, dest, first, s));
         return BMM_OK;
@@ -188,6 +207,7 @@ bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* op
     p.k = k;
     p.n = n;
     if (o.variant < 0 || o.variant > 2) return BMM_ERR_INVALID;
+    if (o.kernel_level < 0 || o.kernel_level > 1) return BMM_ERR_INVALID;
     p.variant = o.variant;
     if (o.path < BMM_PATH_AUTO || o.path > BMM_PATH_TC_FP4_PAIR) return BMM_ERR_INVALID;
     if (is_tc_path(o.path) && !tc_path_available()) return BMM_ERR_UNSUPPORTED;
@@ -212,7 +232,7 @@ bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* op
     // A tuned choice (bmm_autotune) replaces the rules below when both the
     // path and the depth are left to the library.
     int tpath = 0, tdepth = 0;
-    const bool tuned = o.path == BMM_PATH_AUTO && o.strassen_depth < 0 &&
+    const bool tuned = o.path == BMM_PATH_AUTO && o.strassen_depth < 0 && o.kernel_level == 0 &&
                        tuned_choice(op, m, k, n, &tpath, &tdepth) &&
                        (tdepth == 0 || (op == OP_GF2 && divisible(m, k, n, tdepth)));
     if (tuned) {
@@ -227,22 +247,27 @@ bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* op
         const int64_t unit = (int64_t)128 << p.depth;  // leaf k a multiple of 128 bits
         p.kp = (k + unit - 1) / unit * unit;
     }
-    // depth-first levels: at least depth - MAX_MERGED; more while the
+    // The innermost level inside the base-case kernel: the CUDA-core kernel
+    // has that form; a plan without Strassen levels has no level to move.
+    p.kernel_level = (o.kernel_level && p.depth > 0) ? 1 : 0;
+    if (p.kernel_level && p.path != BMM_PATH_POPC) return BMM_ERR_UNSUPPORTED;
+    const int od = p.depth - p.kernel_level;  // levels run by the XOR passes
+    // depth-first levels: at least od - MAX_MERGED; more while the
     // breadth-first scratch does not fit in free device memory.
-    int serial_min = p.depth > MAX_MERGED ? p.depth - MAX_MERGED : 0;
+    int serial_min = od > MAX_MERGED ? od - MAX_MERGED : 0;
     if (o.serial_depth >= 0) {
-        if (o.serial_depth > p.depth) return BMM_ERR_INVALID;
+        if (o.serial_depth > od) return BMM_ERR_INVALID;
         p.serial = o.serial_depth < serial_min ? serial_min : o.serial_depth;
     } else {
         p.serial = serial_min;
         size_t fr = 0, tot = 0;
         if (!(o.workspace) && cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
-            while (p.serial < p.depth &&
-                   workspace_padded(m, k, p.kp, n, p.depth, p.serial) > (uint64_t)(fr * 0.9))
+            while (p.serial < od &&
+                   workspace_padded(m, k, p.kp, n, od, p.serial) > (uint64_t)(fr * 0.9))
                 p.serial++;
         }
     }
-    p.workspace_bytes = workspace_padded(m, k, p.kp, n, p.depth, p.serial);
+    p.workspace_bytes = workspace_padded(m, k, p.kp, n, od, p.serial);
     *out = p;
     return BMM_OK;
 }
@@ -255,8 +280,8 @@ uint64_t plan_pass_bytes(const Plan& p) {
         default: slp::level_masks<2>(xi, eta, zeta); break;
     }
     auto bits = [](uint32_t x) { return (uint64_t)__builtin_popcount(x); };
-    const int dp = p.depth - p.serial, d = p.depth;
-    const bool fused = fused_last_serial(p.depth, p.serial);
+    const int d = p.depth - p.kernel_level, dp = d - p.serial;
+    const bool fused = fused_last_serial(d, p.serial);
     const uint64_t r = (uint64_t)ipow7(dp > 0 ? dp : 0);
     const uint64_t la = (uint64_t)(p.m >> d) * (p.kp >> d) / 8;
     const uint64_t lb = (uint64_t)(p.n >> d) * (p.kp >> d) / 8;

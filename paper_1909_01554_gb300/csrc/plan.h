@@ -14,6 +14,7 @@ struct Plan {
     int variant = BMM_VARIANT_SELF_INVERSE;
     int depth = 0;             // total Strassen levels (0 = cubic)
     int serial = 0;            // of which depth-first (top) levels
+    int kernel_level = 0;      // 1: the innermost level runs inside the base-case kernel
     int64_t m = 0, k = 0, n = 0;
     // k the kernels run with: the tensor-core paths need every leaf's k to be
     // a multiple of 128 bits, so k is rounded up with zero columns of A and

@@ -26,6 +26,8 @@ constexpr int KW64 = 4;    // 64-bit words of k per stage (256 bits)
 constexpr int LD = 12;     // padded shared row in 32-bit words (48 bytes)
 constexpr int STAGES = 3;
 constexpr int SMEM_BYTES = STAGES * (BM + BN) * LD * 4;
+constexpr int LEVEL_STAGES = 2;  // the in-kernel level's ring (filled through registers)
+constexpr int LEVEL_SMEM_BYTES = LEVEL_STAGES * (BM + BN) * LD * 4;
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, int src_bytes) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
@@ -39,6 +41,59 @@ __device__ __forceinline__ void cp_async_commit() {
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One k stage of the CTA's tile: 2 x 4 words of k per thread, 64 LOP3 per
+// four 16-byte shared loads per operand row.
+template <int OP>
+__device__ __forceinline__ void tile_stage(const uint32_t* a_s, const uint32_t* b_s, int tx, int ty,
+                                           uint32_t (&acc)[8][8]) {
+#pragma unroll
+    for (int kk = 0; kk < 2 * KW64; kk += 4) {
+        uint4 a[8], b[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+            a[i] = *reinterpret_cast<const uint4*>(&a_s[(ty + 16 * i) * LD + kk]);
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            b[j] = *reinterpret_cast<const uint4*>(&b_s[(tx + 16 * j) * LD + kk]);
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                if (OP == OP_GF2) {
+                    acc[i][j] ^= a[i].x & b[j].x;
+                    acc[i][j] ^= a[i].y & b[j].y;
+                    acc[i][j] ^= a[i].z & b[j].z;
+                    acc[i][j] ^= a[i].w & b[j].w;
+                } else {
+                    acc[i][j] |= a[i].x & b[j].x;
+                    acc[i][j] |= a[i].y & b[j].y;
+                    acc[i][j] |= a[i].z & b[j].z;
+                    acc[i][j] |= a[i].w & b[j].w;
+                }
+            }
+    }
+}
+
+// Epilogue gather. Lanes 0-15 of a warp hold row ty0 = 2*warp, lanes 16-31
+// row ty0+1; lane tx holds column tx + 16 j. One ballot per (i, j) yields 16
+// bits of two rows; lane L keeps the 64-bit word (i = L/4, row half (L/2)%2,
+// word L%2) of the tile, at tile row 2*warp + half + 16*i, tile word L%2.
+template <int OP>
+__device__ __forceinline__ uint64_t tile_word(const uint32_t (&acc)[8][8], int lane) {
+    uint64_t myword = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const bool bit = (OP == OP_GF2) ? ((__popc(acc[i][j]) & 1) != 0) : (acc[i][j] != 0u);
+            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+            const int w = j >> 2, sh = 16 * (j & 3);
+            if (lane == i * 4 + 0 + w) myword |= (uint64_t)(bal & 0xffffu) << sh;
+            if (lane == i * 4 + 2 + w) myword |= (uint64_t)(bal >> 16) << sh;
+        }
+    return myword;
 }
 
 template <int OP>
@@ -99,57 +154,132 @@ __global__ void __launch_bounds__(256, 1)
             if (nt < nk) load_stage(nt % STAGES, nt);
             cp_async_commit();
         }
-        const uint32_t* a_s = sA + (kt % STAGES) * BM * LD;
-        const uint32_t* b_s = sB + (kt % STAGES) * BN * LD;
-#pragma unroll
-        for (int kk = 0; kk < 2 * KW64; kk += 4) {
-            uint4 a[8], b[8];
-#pragma unroll
-            for (int i = 0; i < 8; i++)
-                a[i] = *reinterpret_cast<const uint4*>(&a_s[(ty + 16 * i) * LD + kk]);
-#pragma unroll
-            for (int j = 0; j < 8; j++)
-                b[j] = *reinterpret_cast<const uint4*>(&b_s[(tx + 16 * j) * LD + kk]);
-#pragma unroll
-            for (int i = 0; i < 8; i++)
-#pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    if (OP == OP_GF2) {
-                        acc[i][j] ^= a[i].x & b[j].x;
-                        acc[i][j] ^= a[i].y & b[j].y;
-                        acc[i][j] ^= a[i].z & b[j].z;
-                        acc[i][j] ^= a[i].w & b[j].w;
-                    } else {
-                        acc[i][j] |= a[i].x & b[j].x;
-                        acc[i][j] |= a[i].y & b[j].y;
-                        acc[i][j] |= a[i].z & b[j].z;
-                        acc[i][j] |= a[i].w & b[j].w;
-                    }
-                }
-        }
+        tile_stage<OP>(sA + (kt % STAGES) * BM * LD, sB + (kt % STAGES) * BN * LD, tx, ty, acc);
     }
     cp_async_wait<0>();
 
-    // Epilogue. Lanes 0-15 of a warp hold row ty0 = 2*warp, lanes 16-31 row ty0+1;
-    // lane tx holds column tx + 16 j. One ballot per (i, j) yields 16 bits of two
-    // rows; lane L keeps the 64-bit word (i = L/4, row half (L/2)%2, word L%2).
     const int warp = tid >> 5, lane = tid & 31;
-    uint64_t myword = 0;
-#pragma unroll
-    for (int i = 0; i < 8; i++)
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const bool bit = (OP == OP_GF2) ? ((__popc(acc[i][j]) & 1) != 0) : (acc[i][j] != 0u);
-            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-            const int w = j >> 2, sh = 16 * (j & 3);
-            if (lane == i * 4 + 0 + w) myword |= (uint64_t)(bal & 0xffffu) << sh;
-            if (lane == i * 4 + 2 + w) myword |= (uint64_t)(bal >> 16) << sh;
-        }
+    const uint64_t myword = tile_word<OP>(acc, lane);
     {
         const int i = lane >> 2, half = (lane >> 1) & 1, w = lane & 1;
         const int64_t row = row0 + 2 * warp + half + 16 * i;
         const int64_t cw = col0 / 64 + w;
         if (row < m && cw < n / 64) C[row * ldc + cw] = myword;
+    }
+}
+
+// One Strassen level inside the kernel (the GEMM-side form of a recursion
+// level, Sec. 3.9 with the base case of Sec. 3.10 beneath it): the binary
+// product C (2hm x 2hn) = A (2hm x 2hk) * Bt (2hn x 2hk)^T of one block,
+// through its seven quadrant-sized products. The CTA owns one 128 x 128
+// tile position of the quadrant-sized product and runs the seven products
+// there one after the other. Product h reads, per word of k, the quadrants
+// of A that xi_h selects and the quadrants of B that eta_h selects, XORed
+// together as they are staged into shared memory (the combined input
+// operators xi = alpha phi and eta = beta psi of one level), so its operands
+// never exist in HBM. Its result bits are XORed into each C quadrant that
+// zeta = chi gamma sends it to, in registers; the four quadrant words leave
+// once, after the seventh product. The stage ring is two buffers filled
+// through registers (a ld.global per selected quadrant, then one shared
+// store), with the next stage's loads in flight during the current stage.
+__global__ void __launch_bounds__(256, 1)
+    popc_level_kernel(const uint64_t* __restrict__ A, int64_t lda, int64_t strideA,
+                      const uint64_t* __restrict__ Bt, int64_t ldb, int64_t strideB,
+                      uint64_t* __restrict__ C, int64_t ldc, int64_t strideC, int64_t hm,
+                      int64_t hk, int64_t hn, uint32_t xi4, uint32_t eta4, uint32_t zeta7) {
+    A += (int64_t)blockIdx.z * strideA;
+    Bt += (int64_t)blockIdx.z * strideB;
+    C += (int64_t)blockIdx.z * strideC;
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t* sA = smem;                           // [LEVEL_STAGES][BM][LD]
+    uint32_t* sB = smem + LEVEL_STAGES * BM * LD;  // [LEVEL_STAGES][BN][LD]
+
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int64_t row0 = (int64_t)blockIdx.y * BM, col0 = (int64_t)blockIdx.x * BN;
+    const int64_t hkw = hk / 64;  // words of k per quadrant
+    const int nk = (int)((hkw + KW64 - 1) / KW64);
+
+    // word offsets of the quadrants: A block (i, j) at rows i*hm, words
+    // j*hkw; B block (i, j) is stored transposed in Bt, at rows j*hn, words
+    // i*hkw (block q = 2i + j)
+    int64_t aoff[4], boff[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        aoff[q] = (q >> 1) * hm * lda + (q & 1) * hkw;
+        boff[q] = (q & 1) * hn * ldb + (q >> 1) * hkw;
+    }
+    uint64_t out[4] = {0, 0, 0, 0};  // this thread's word of each C quadrant
+    for (int h = 0; h < 7; h++) {
+        const uint32_t xa = (xi4 >> (4 * h)) & 0xFu, xb = (eta4 >> (4 * h)) & 0xFu;
+        uint64_t ra[2], rb[2];
+        auto fetch = [&](int kt) {
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                const int c = tid + u * 256;  // 512 words of 8 bytes per operand
+                const int r = c >> 2, w = c & 3;
+                const int64_t kw = (int64_t)kt * KW64 + w;
+                uint64_t a = 0, b = 0;
+                if (kw < hkw && row0 + r < hm) {
+                    const uint64_t* src = A + (row0 + r) * lda + kw;
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        if ((xa >> q) & 1u) a ^= __ldg(src + aoff[q]);
+                }
+                if (kw < hkw && col0 + r < hn) {
+                    const uint64_t* src = Bt + (col0 + r) * ldb + kw;
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        if ((xb >> q) & 1u) b ^= __ldg(src + boff[q]);
+                }
+                ra[u] = a;
+                rb[u] = b;
+            }
+        };
+        auto stash = [&](int s) {
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                const int c = tid + u * 256;
+                const int r = c >> 2, w = c & 3;
+                *reinterpret_cast<uint64_t*>(&sA[(s * BM + r) * LD + 2 * w]) = ra[u];
+                *reinterpret_cast<uint64_t*>(&sB[(s * BN + r) * LD + 2 * w]) = rb[u];
+            }
+        };
+
+        uint32_t acc[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+#pragma unroll
+            for (int j = 0; j < 8; j++) acc[i][j] = 0u;
+        // The previous product's last stage ended at a barrier, so buffer 0
+        // is free.
+        fetch(0);
+        stash(0);
+        __syncthreads();
+        for (int kt = 0; kt < nk; kt++) {
+            const bool more = kt + 1 < nk;
+            if (more) fetch(kt + 1);
+            tile_stage<OP_GF2>(sA + (kt & 1) * BM * LD, sB + (kt & 1) * BN * LD, tx, ty, acc);
+            // buffer (kt+1)&1 was last read in stage kt-1, which every thread
+            // finished before the barrier that ended it
+            if (more) stash((kt + 1) & 1);
+            __syncthreads();
+        }
+        const uint64_t word = tile_word<OP_GF2>(acc, lane);
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if ((zeta7 >> (7 * q + h)) & 1u) out[q] ^= word;
+    }
+    {
+        const int i = lane >> 2, half = (lane >> 1) & 1, w = lane & 1;
+        const int64_t row = row0 + 2 * warp + half + 16 * i;
+        const int64_t cw = col0 / 64 + w;
+        const int64_t hnw = hn / 64;
+        if (row < hm && cw < hnw) {
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                C[((q >> 1) * hm + row) * ldc + (q & 1) * hnw + cw] = out[q];
+        }
     }
 }
 
@@ -171,6 +301,32 @@ cudaError_t launch_popc_nt(int op, const uint64_t* A, int64_t lda, int64_t strid
     else
         popc_nt_kernel<OP_BOOL><<<grid, 256, SMEM_BYTES, s>>>(A, lda, strideA, Bt, ldb, strideB,
                                                               C, ldc, strideC, m, k, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_popc_level(const uint64_t* A, int64_t lda, int64_t strideA, const uint64_t* Bt,
+                              int64_t ldb, int64_t strideB, uint64_t* C, int64_t ldc,
+                              int64_t strideC, int64_t count, int64_t m, int64_t k, int64_t n,
+                              const LevelMasks& masks, cudaStream_t s) {
+    if (m % 2 || k % 128 || n % 128) return cudaErrorInvalidValue;
+    const int64_t hm = m / 2, hk = k / 2, hn = n / 2;
+    const int64_t gx = (hn + BN - 1) / BN, gy = (hm + BM - 1) / BM;
+    if (gx <= 0 || gy <= 0 || count <= 0) return cudaSuccess;
+    if (gy > 65535 || count > 65535) return cudaErrorInvalidConfiguration;
+    const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)count);
+    static_assert(LEVEL_SMEM_BYTES <= 48 * 1024, "fits the default dynamic shared memory limit");
+    // the masks packed into three words: nibble h of xi4 / eta4 = xi[h] /
+    // eta[h]; bits 7q..7q+6 of zeta7 = zeta[q]
+    uint32_t xi4 = 0, eta4 = 0, zeta7 = 0;
+    for (int h = 0; h < 7; h++) {
+        xi4 |= (masks.xi[h] & 0xFu) << (4 * h);
+        eta4 |= (masks.eta[h] & 0xFu) << (4 * h);
+    }
+    for (int q = 0; q < 4; q++) zeta7 |= (masks.zeta[q] & 0x7Fu) << (7 * q);
+    TraceScope ts(BMM_PHASE_BASE, s);
+    popc_level_kernel<<<grid, 256, LEVEL_SMEM_BYTES, s>>>(A, lda, strideA, Bt, ldb, strideB, C,
+                                                          ldc, strideC, hm, hk, hn, xi4, eta4,
+                                                          zeta7);
     return cudaGetLastError();
 }
 

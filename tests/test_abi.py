@@ -140,3 +140,54 @@ def test_host_product_argument_checks_need_no_gpu(built_lib):
     info = bmm.HostPlanInfo()
     assert L.bmm_host_plan(2, 64, 64, 64, ctypes.byref(o), ctypes.byref(info)) == bmm.ERR_INVALID
     assert L.bmm_host_plan(0, 64, 64, 64, ctypes.byref(o), None) == bmm.ERR_INVALID
+
+
+def test_kernel_level_plans_need_no_gpu(built_lib):
+    """With the innermost Strassen level inside the CUDA-core kernel, the XOR
+    passes run one level fewer: the plan's scratch is that of the plan one
+    level shallower (no leaf operands or products of the last level), its
+    depth-first levels are capped one lower, and the option is refused where
+    it cannot apply."""
+    import paper_1909_01554_gb300 as bmm
+
+    m = k = n = 8192
+    for d in (1, 2, 3, 4):
+        kl = bmm.plan(bmm.GF2, m, k, n, path=bmm.PATH_POPC, depth=d, kernel_level=1)
+        assert kl["kernel_level"] == 1 and kl["strassen_depth"] == d
+        assert kl["leaves"] == 7 ** d
+        flat = bmm.plan(bmm.GF2, m, k, n, path=bmm.PATH_POPC, depth=d - 1,
+                        serial=kl["serial_depth"])
+        assert kl["workspace_bytes"] == flat["workspace_bytes"]
+        assert kl["serial_depth"] <= d - 1
+        # the same depth-first split with every level in XOR passes needs more
+        whole = bmm.plan(bmm.GF2, m, k, n, path=bmm.PATH_POPC, depth=d,
+                         serial=kl["serial_depth"])
+        assert whole["kernel_level"] == 0
+        if whole["serial_depth"] == kl["serial_depth"]:  # else XOR passes merge too few
+            assert kl["workspace_bytes"] < whole["workspace_bytes"]
+    # depth 1: the only scratch is B^T
+    assert bmm.plan(bmm.GF2, m, k, n, path=bmm.PATH_POPC, depth=1,
+                    kernel_level=1)["workspace_bytes"] == k * n // 8
+    # nothing to move: cubic plans and the Boolean product ignore it
+    assert bmm.plan(bmm.GF2, m, k, n, path=bmm.PATH_POPC, depth=0,
+                    kernel_level=1)["kernel_level"] == 0
+    assert bmm.plan(bmm.BOOL, m, k, n, path=bmm.PATH_POPC, kernel_level=1)["kernel_level"] == 0
+    L = bmm.lib()
+    info = bmm.PlanInfo()
+    for bad in (-1, 2):
+        o = bmm.opts(path=bmm.PATH_POPC, depth=2, kernel_level=bad)
+        assert L.bmm_plan(bmm.GF2, m, k, n, ctypes_ref(o), ctypes_ref(info)) == bmm.ERR_INVALID
+    # every depth-first level would leave none for the kernel
+    o = bmm.opts(path=bmm.PATH_POPC, depth=2, serial=2, kernel_level=1)
+    assert L.bmm_plan(bmm.GF2, m, k, n, ctypes_ref(o), ctypes_ref(info)) == bmm.ERR_INVALID
+    # the tensor-core kernels have no in-kernel level
+    for path in bmm.TENSOR_PATHS:
+        o = bmm.opts(path=path, depth=2, kernel_level=1)
+        assert L.bmm_plan(bmm.GF2, m, k, n, ctypes_ref(o),
+                          ctypes_ref(info)) == bmm.ERR_UNSUPPORTED
+
+
+def ctypes_ref(x):
+    import ctypes
+
+    return ctypes.byref(x)

@@ -218,6 +218,41 @@ def test_strassen_variants(variant, depth, serial):
     check(got, want, f"strassen v={variant} d={depth} s={serial}")
 
 
+# The innermost level inside the CUDA-core kernel. m, k, n = (320, 576, 448)
+# << depth: the in-kernel quadrants are 2.5 x 3.5 tiles of 128 and 9 words of
+# k (two full stages of 4 and a ragged one).
+@pytest.mark.parametrize("variant", [bmm.WINOGRAD, bmm.SELF_INVERSE, bmm.CHAINING])
+@pytest.mark.parametrize("depth,serial", [(1, 0), (2, 0), (2, 1), (3, 1), (3, 2)])
+def test_kernel_level(variant, depth, serial):
+    m, k, n = 320 << depth, 576 << depth, 448 << depth
+    Ah, Bh = gen(m, k, 29, 0), gen(k, n, 29, 1)
+    want = O.cubic(O.GF2, Ah, Bh, m, k, n)
+    info = bmm.plan(bmm.GF2, m, k, n, depth=depth, serial=serial, variant=variant,
+                    path=bmm.PATH_POPC, kernel_level=1)
+    assert info["kernel_level"] == 1 and info["serial_depth"] == serial
+    got = run(bmm.GF2, Ah, Bh, m, k, n, depth=depth, serial=serial, variant=variant,
+              path=bmm.PATH_POPC, kernel_level=1)
+    check(got, want, f"kernel level v={variant} d={depth} s={serial}")
+
+
+def test_kernel_level_degenerate_and_unsupported():
+    """All-ones operands (every product's operand combination is all ones or
+    zero), the identity, and the tensor paths' refusal."""
+    m = k = n = 1024
+    ones = np.full((m, k // 64), np.uint64(0xFFFFFFFFFFFFFFFF), dtype=np.uint64)
+    want = O.cubic(O.GF2, ones, ones, m, k, n)
+    got = run(bmm.GF2, ones, ones, m, k, n, depth=2, path=bmm.PATH_POPC, kernel_level=1)
+    check(got, want, "kernel level, all ones")
+    eye = O.pack(np.eye(n, dtype=np.uint8))
+    A = gen(m, k, 31, 0)
+    check(run(bmm.GF2, A, eye, m, k, n, depth=1, path=bmm.PATH_POPC, kernel_level=1), A,
+          "kernel level, A I")
+    if bmm.device_supported():
+        for path in bmm.TENSOR_PATHS:
+            with pytest.raises(bmm.BmmError):
+                run(bmm.GF2, ones, ones, m, k, n, depth=2, path=path, kernel_level=1)
+
+
 @pytest.mark.parametrize("path", paths())
 def test_strassen_over_each_base_case(path):
     n = 2048

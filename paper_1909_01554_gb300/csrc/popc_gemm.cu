@@ -16,6 +16,8 @@
 // loads of 16 bytes. Rows are padded to 48 bytes, which keeps every
 // quarter-warp's 128-bit loads on distinct banks. The epilogue gathers the
 // result bits of a warp with ballots and writes whole 64-bit words.
+#include <mutex>
+
 #include "internal.h"
 
 namespace bmm {
@@ -25,9 +27,13 @@ constexpr int BM = 128, BN = 128;
 constexpr int KW64 = 4;    // 64-bit words of k per stage (256 bits)
 constexpr int LD = 12;     // padded shared row in 32-bit words (48 bytes)
 constexpr int STAGES = 3;
+constexpr int MAX_DEVICES = 64;  // per-device one-time kernel attributes
 constexpr int SMEM_BYTES = STAGES * (BM + BN) * LD * 4;
-constexpr int LEVEL_STAGES = 2;  // the in-kernel level's ring (filled through registers)
-constexpr int LEVEL_SMEM_BYTES = LEVEL_STAGES * (BM + BN) * LD * 4;
+// The in-kernel level: double-buffered operand tiles, and a ring of raw
+// quadrant words (2 words x 2 operands x 4 quadrants per thread and stage).
+constexpr int LEVEL_STAGES = 2;
+constexpr int RAW_SLOTS = 3;
+constexpr int LEVEL_SMEM_BYTES = LEVEL_STAGES * (BM + BN) * LD * 4 + RAW_SLOTS * 2 * 2 * 4 * 256 * 8;
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, int src_bytes) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
@@ -174,14 +180,19 @@ __global__ void __launch_bounds__(256, 1)
 // through its seven quadrant-sized products. The CTA owns one 128 x 128
 // tile position of the quadrant-sized product and runs the seven products
 // there one after the other. Product h reads, per word of k, the quadrants
-// of A that xi_h selects and the quadrants of B that eta_h selects, XORed
-// together as they are staged into shared memory (the combined input
-// operators xi = alpha phi and eta = beta psi of one level), so its operands
-// never exist in HBM. Its result bits are XORed into each C quadrant that
-// zeta = chi gamma sends it to, in registers; the four quadrant words leave
-// once, after the seventh product. The stage ring is two buffers filled
-// through registers (a ld.global per selected quadrant, then one shared
-// store), with the next stage's loads in flight during the current stage.
+// of A that xi_h selects and the quadrants of B that eta_h selects and XORs
+// them as they are staged (the combined input operators xi = alpha phi and
+// eta = beta psi of one level), so its operands never exist in HBM. Its
+// result bits are XORed into each C quadrant that zeta = chi gamma sends it
+// to, in registers; the four quadrant words leave once, after the seventh
+// product.
+//
+// Staging: each thread copies its own words of every selected quadrant with
+// cp.async into a ring of RAW_SLOTS stages laid out per thread (consecutive
+// threads, consecutive 8-byte words: conflict-free), two stages ahead of
+// the compute; once its own copies of a stage have landed (wait_group, no
+// barrier needed), it XORs them and stores the combined word into the
+// double-buffered operand tile that the LOP3 loop reads.
 __global__ void __launch_bounds__(256, 1)
     popc_level_kernel(const uint64_t* __restrict__ A, int64_t lda, int64_t strideA,
                       const uint64_t* __restrict__ Bt, int64_t ldb, int64_t strideB,
@@ -193,12 +204,17 @@ __global__ void __launch_bounds__(256, 1)
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t* sA = smem;                           // [LEVEL_STAGES][BM][LD]
     uint32_t* sB = smem + LEVEL_STAGES * BM * LD;  // [LEVEL_STAGES][BN][LD]
+    // [RAW_SLOTS][2 words u][2 operands][4 quadrants][256 threads]
+    uint64_t* raw = reinterpret_cast<uint64_t*>(smem + LEVEL_STAGES * (BM + BN) * LD);
 
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int warp = tid >> 5, lane = tid & 31;
     const int64_t row0 = (int64_t)blockIdx.y * BM, col0 = (int64_t)blockIdx.x * BN;
     const int64_t hkw = hk / 64;  // words of k per quadrant
     const int nk = (int)((hkw + KW64 - 1) / KW64);
+    auto raw_at = [&](int slot, int u, int op, int q) {
+        return raw + ((((slot * 2 + u) * 2 + op) * 4 + q) * 256 + tid);
+    };
 
     // word offsets of the quadrants: A block (i, j) at rows i*hm, words
     // j*hkw; B block (i, j) is stored transposed in Bt, at rows j*hn, words
@@ -212,37 +228,43 @@ __global__ void __launch_bounds__(256, 1)
     uint64_t out[4] = {0, 0, 0, 0};  // this thread's word of each C quadrant
     for (int h = 0; h < 7; h++) {
         const uint32_t xa = (xi4 >> (4 * h)) & 0xFu, xb = (eta4 >> (4 * h)) & 0xFu;
-        uint64_t ra[2], rb[2];
-        auto fetch = [&](int kt) {
+        // this thread's words (row r, word w of the stage) of every selected
+        // quadrant of stage kt, copied into ring slot kt % RAW_SLOTS
+        auto issue = [&](int kt) {
+            const int slot = kt % RAW_SLOTS;
 #pragma unroll
             for (int u = 0; u < 2; u++) {
                 const int c = tid + u * 256;  // 512 words of 8 bytes per operand
                 const int r = c >> 2, w = c & 3;
                 const int64_t kw = (int64_t)kt * KW64 + w;
-                uint64_t a = 0, b = 0;
-                if (kw < hkw && row0 + r < hm) {
-                    const uint64_t* src = A + (row0 + r) * lda + kw;
+                const bool oka = kw < hkw && row0 + r < hm;
+                const bool okb = kw < hkw && col0 + r < hn;
+                const uint64_t* sa = A + (oka ? (row0 + r) * lda + kw : 0);
+                const uint64_t* sb = Bt + (okb ? (col0 + r) * ldb + kw : 0);
 #pragma unroll
-                    for (int q = 0; q < 4; q++)
-                        if ((xa >> q) & 1u) a ^= __ldg(src + aoff[q]);
+                for (int q = 0; q < 4; q++) {
+                    if ((xa >> q) & 1u)
+                        cp_async8(raw_at(slot, u, 0, q), oka ? sa + aoff[q] : A, oka ? 8 : 0);
+                    if ((xb >> q) & 1u)
+                        cp_async8(raw_at(slot, u, 1, q), okb ? sb + boff[q] : Bt, okb ? 8 : 0);
                 }
-                if (kw < hkw && col0 + r < hn) {
-                    const uint64_t* src = Bt + (col0 + r) * ldb + kw;
-#pragma unroll
-                    for (int q = 0; q < 4; q++)
-                        if ((xb >> q) & 1u) b ^= __ldg(src + boff[q]);
-                }
-                ra[u] = a;
-                rb[u] = b;
             }
         };
-        auto stash = [&](int s) {
+        // stage kt's words (landed) XORed into operand buffer `buf`
+        auto combine = [&](int kt, int buf) {
+            const int slot = kt % RAW_SLOTS;
 #pragma unroll
             for (int u = 0; u < 2; u++) {
                 const int c = tid + u * 256;
                 const int r = c >> 2, w = c & 3;
-                *reinterpret_cast<uint64_t*>(&sA[(s * BM + r) * LD + 2 * w]) = ra[u];
-                *reinterpret_cast<uint64_t*>(&sB[(s * BN + r) * LD + 2 * w]) = rb[u];
+                uint64_t a = 0, b = 0;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if ((xa >> q) & 1u) a ^= *raw_at(slot, u, 0, q);
+                    if ((xb >> q) & 1u) b ^= *raw_at(slot, u, 1, q);
+                }
+                *reinterpret_cast<uint64_t*>(&sA[(buf * BM + r) * LD + 2 * w]) = a;
+                *reinterpret_cast<uint64_t*>(&sB[(buf * BN + r) * LD + 2 * w]) = b;
             }
         };
 
@@ -251,18 +273,27 @@ __global__ void __launch_bounds__(256, 1)
         for (int i = 0; i < 8; i++)
 #pragma unroll
             for (int j = 0; j < 8; j++) acc[i][j] = 0u;
-        // The previous product's last stage ended at a barrier, so buffer 0
-        // is free.
-        fetch(0);
-        stash(0);
+        // Every copy group of the previous product has been waited for, and
+        // its last stage ended at a barrier: the ring and buffer 0 are free.
+        issue(0);
+        cp_async_commit();
+        if (nk > 1) issue(1);
+        cp_async_commit();
+        cp_async_wait<1>();  // stage 0
+        combine(0, 0);
         __syncthreads();
         for (int kt = 0; kt < nk; kt++) {
-            const bool more = kt + 1 < nk;
-            if (more) fetch(kt + 1);
+            // slot (kt+2) % RAW_SLOTS held stage kt-1, combined in the
+            // previous iteration by this same thread
+            if (kt + 2 < nk) issue(kt + 2);
+            cp_async_commit();
             tile_stage<OP_GF2>(sA + (kt & 1) * BM * LD, sB + (kt & 1) * BN * LD, tx, ty, acc);
-            // buffer (kt+1)&1 was last read in stage kt-1, which every thread
-            // finished before the barrier that ended it
-            if (more) stash((kt + 1) & 1);
+            if (kt + 1 < nk) {
+                cp_async_wait<1>();  // stage kt+1 (only stage kt+2 may be in flight)
+                // buffer (kt+1)&1 was last read in stage kt-1, which every
+                // thread finished before the barrier that ended it
+                combine(kt + 1, (kt + 1) & 1);
+            }
             __syncthreads();
         }
         const uint64_t word = tile_word<OP_GF2>(acc, lane);
@@ -314,7 +345,23 @@ cudaError_t launch_popc_level(const uint64_t* A, int64_t lda, int64_t strideA, c
     if (gx <= 0 || gy <= 0 || count <= 0) return cudaSuccess;
     if (gy > 65535 || count > 65535) return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)count);
-    static_assert(LEVEL_SMEM_BYTES <= 48 * 1024, "fits the default dynamic shared memory limit");
+    static_assert(LEVEL_SMEM_BYTES <= 227 * 1024, "fits one CTA's shared memory");
+    {
+        static bool done[MAX_DEVICES] = {false};
+        static cudaError_t err[MAX_DEVICES];
+        static std::mutex mu;
+        int d = 0;
+        if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= MAX_DEVICES)
+            return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lk(mu);
+        if (!done[d]) {
+            err[d] = cudaFuncSetAttribute(popc_level_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          LEVEL_SMEM_BYTES);
+            done[d] = true;
+        }
+        if (err[d] != cudaSuccess) return err[d];
+    }
     // the masks packed into three words: nibble h of xi4 / eta4 = xi[h] /
     // eta[h]; bits 7q..7q+6 of zeta7 = zeta[q]
     uint32_t xi4 = 0, eta4 = 0, zeta7 = 0;

@@ -235,6 +235,15 @@ def test_kernel_level(variant, depth, serial):
     check(got, want, f"kernel level v={variant} d={depth} s={serial}")
 
 
+@pytest.mark.parametrize("m,k,n", [(384, 2688, 640), (256, 4096, 256)])
+def test_kernel_level_long_k(m, k, n):
+    """Quadrants of 21 and 32 words of k: the staging ring wraps several times."""
+    Ah, Bh = gen(m, k, 37, 0), gen(k, n, 37, 1)
+    want = O.cubic(O.GF2, Ah, Bh, m, k, n)
+    got = run(bmm.GF2, Ah, Bh, m, k, n, depth=1, path=bmm.PATH_POPC, kernel_level=1)
+    check(got, want, f"kernel level {m}x{k}x{n}")
+
+
 def test_kernel_level_degenerate_and_unsupported():
     """All-ones operands (every product's operand combination is all ones or
     zero), the identity, and the tensor paths' refusal."""

@@ -35,9 +35,24 @@ constexpr int LEVEL_STAGES = 2;
 constexpr int RAW_SLOTS = 3;
 constexpr int LEVEL_SMEM_BYTES = LEVEL_STAGES * (BM + BN) * LD * 4 + RAW_SLOTS * 2 * 2 * 4 * 256 * 8;
 
+// 64-bit words of a stage row (KW64) that one thread copies: VW = 2 (16-byte
+// copies, two threads per row) where every copied pair is 16-byte aligned,
+// else VW = 1 (8-byte copies, four threads per row, two rows per thread).
+template <int VW>
+struct LevelMap {
+    static constexpr int TPR = KW64 / VW;   // threads per stage row
+    static constexpr int U = TPR / 2;       // rows per thread (256 threads, 128 rows)
+};
+
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, int src_bytes) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc),
                  "r"(src_bytes)
                  : "memory");
 }
@@ -189,23 +204,28 @@ __global__ void __launch_bounds__(256, 1)
 //
 // Staging: each thread copies its own words of every selected quadrant with
 // cp.async into a ring of RAW_SLOTS stages laid out per thread (consecutive
-// threads, consecutive 8-byte words: conflict-free), two stages ahead of
-// the compute; once its own copies of a stage have landed (wait_group, no
-// barrier needed), it XORs them and stores the combined word into the
-// double-buffered operand tile that the LOP3 loop reads.
+// threads, consecutive words: conflict-free), two stages ahead of the
+// compute; once its own copies of a stage have landed (wait_group, no
+// barrier needed), it XORs them and stores the combined words into the
+// double-buffered operand tile that the LOP3 loop reads. The source
+// addresses are formed once per product and advance by one stage per step.
+template <int VW>
 __global__ void __launch_bounds__(256, 1)
     popc_level_kernel(const uint64_t* __restrict__ A, int64_t lda, int64_t strideA,
                       const uint64_t* __restrict__ Bt, int64_t ldb, int64_t strideB,
                       uint64_t* __restrict__ C, int64_t ldc, int64_t strideC, int64_t hm,
                       int64_t hk, int64_t hn, uint32_t xi4, uint32_t eta4, uint32_t zeta7) {
+    using LM = LevelMap<VW>;
+    constexpr int U = LM::U, TPR = LM::TPR;
     A += (int64_t)blockIdx.z * strideA;
     Bt += (int64_t)blockIdx.z * strideB;
     C += (int64_t)blockIdx.z * strideC;
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t* sA = smem;                           // [LEVEL_STAGES][BM][LD]
     uint32_t* sB = smem + LEVEL_STAGES * BM * LD;  // [LEVEL_STAGES][BN][LD]
-    // [RAW_SLOTS][2 words u][2 operands][4 quadrants][256 threads]
+    // [RAW_SLOTS][U][2 operands][4 quadrants][256 threads][VW words]
     uint64_t* raw = reinterpret_cast<uint64_t*>(smem + LEVEL_STAGES * (BM + BN) * LD);
+    static_assert(U * VW == 2, "the ring holds two words per thread, operand and quadrant");
 
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int warp = tid >> 5, lane = tid & 31;
@@ -213,40 +233,64 @@ __global__ void __launch_bounds__(256, 1)
     const int64_t hkw = hk / 64;  // words of k per quadrant
     const int nk = (int)((hkw + KW64 - 1) / KW64);
     auto raw_at = [&](int slot, int u, int op, int q) {
-        return raw + ((((slot * 2 + u) * 2 + op) * 4 + q) * 256 + tid);
+        return raw + (((((slot * U + u) * 2 + op) * 4 + q) * 256 + tid) * VW);
     };
 
-    // word offsets of the quadrants: A block (i, j) at rows i*hm, words
-    // j*hkw; B block (i, j) is stored transposed in Bt, at rows j*hn, words
-    // i*hkw (block q = 2i + j)
-    int64_t aoff[4], boff[4];
+    // This thread's rows r and first words w of every stage, and its first
+    // source word in each quadrant: A block (i, j) at rows i*hm, words j*hkw;
+    // B block (i, j) is stored transposed in Bt, at rows j*hn, words i*hkw
+    // (block q = 2i + j). Rows past the block read nothing.
+    int rr[U], ww[U];
+    bool rowa[U], rowb[U];
+    const uint64_t* pa[U][4];
+    const uint64_t* pb[U][4];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-        aoff[q] = (q >> 1) * hm * lda + (q & 1) * hkw;
-        boff[q] = (q & 1) * hn * ldb + (q >> 1) * hkw;
+    for (int u = 0; u < U; u++) {
+        const int c = tid + u * 256;
+        rr[u] = c / TPR;
+        ww[u] = (c % TPR) * VW;
+        rowa[u] = row0 + rr[u] < hm;
+        rowb[u] = col0 + rr[u] < hn;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            pa[u][q] = rowa[u] ? A + (row0 + rr[u] + (q >> 1) * hm) * lda + (q & 1) * hkw + ww[u]
+                               : A;
+            pb[u][q] = rowb[u] ? Bt + (col0 + rr[u] + (q & 1) * hn) * ldb + (q >> 1) * hkw + ww[u]
+                               : Bt;
+        }
     }
+
     uint64_t out[4] = {0, 0, 0, 0};  // this thread's word of each C quadrant
     for (int h = 0; h < 7; h++) {
         const uint32_t xa = (xi4 >> (4 * h)) & 0xFu, xb = (eta4 >> (4 * h)) & 0xFu;
-        // this thread's words (row r, word w of the stage) of every selected
-        // quadrant of stage kt, copied into ring slot kt % RAW_SLOTS
+        // this thread's words of every selected quadrant of stage kt, copied
+        // into ring slot kt % RAW_SLOTS
         auto issue = [&](int kt) {
             const int slot = kt % RAW_SLOTS;
+            const int64_t adv = (int64_t)kt * KW64;
 #pragma unroll
-            for (int u = 0; u < 2; u++) {
-                const int c = tid + u * 256;  // 512 words of 8 bytes per operand
-                const int r = c >> 2, w = c & 3;
-                const int64_t kw = (int64_t)kt * KW64 + w;
-                const bool oka = kw < hkw && row0 + r < hm;
-                const bool okb = kw < hkw && col0 + r < hn;
-                const uint64_t* sa = A + (oka ? (row0 + r) * lda + kw : 0);
-                const uint64_t* sb = Bt + (okb ? (col0 + r) * ldb + kw : 0);
+            for (int u = 0; u < U; u++) {
+                const bool kv = adv + ww[u] < hkw;
+                const bool oka = kv && rowa[u], okb = kv && rowb[u];
+                const int bytes_a = oka ? 8 * VW : 0, bytes_b = okb ? 8 * VW : 0;
+                // a copy that reads nothing still gets an address inside the
+                // operand (its base)
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
-                    if ((xa >> q) & 1u)
-                        cp_async8(raw_at(slot, u, 0, q), oka ? sa + aoff[q] : A, oka ? 8 : 0);
-                    if ((xb >> q) & 1u)
-                        cp_async8(raw_at(slot, u, 1, q), okb ? sb + boff[q] : Bt, okb ? 8 : 0);
+                    if ((xa >> q) & 1u) {
+                        const uint64_t* src = oka ? pa[u][q] + adv : A;
+                        if (VW == 2)
+                            cp_async16(raw_at(slot, u, 0, q), src, bytes_a);
+                        else
+                            cp_async8(raw_at(slot, u, 0, q), src, bytes_a);
+                    }
+                    if ((xb >> q) & 1u) {
+                        const uint64_t* src = okb ? pb[u][q] + adv : Bt;
+                        if (VW == 2)
+                            cp_async16(raw_at(slot, u, 1, q), src, bytes_b);
+                        else
+                            cp_async8(raw_at(slot, u, 1, q), src, bytes_b);
+                    }
                 }
             }
         };
@@ -254,17 +298,42 @@ __global__ void __launch_bounds__(256, 1)
         auto combine = [&](int kt, int buf) {
             const int slot = kt % RAW_SLOTS;
 #pragma unroll
-            for (int u = 0; u < 2; u++) {
-                const int c = tid + u * 256;
-                const int r = c >> 2, w = c & 3;
-                uint64_t a = 0, b = 0;
+            for (int u = 0; u < U; u++) {
+                uint64_t a[VW], b[VW];
+#pragma unroll
+                for (int v = 0; v < VW; v++) a[v] = b[v] = 0;
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
-                    if ((xa >> q) & 1u) a ^= *raw_at(slot, u, 0, q);
-                    if ((xb >> q) & 1u) b ^= *raw_at(slot, u, 1, q);
+                    if ((xa >> q) & 1u) {
+                        const uint64_t* x = raw_at(slot, u, 0, q);
+                        if (VW == 2) {
+                            const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(x);
+                            a[0] ^= t.x;
+                            a[VW - 1] ^= t.y;
+                        } else {
+                            a[0] ^= x[0];
+                        }
+                    }
+                    if ((xb >> q) & 1u) {
+                        const uint64_t* x = raw_at(slot, u, 1, q);
+                        if (VW == 2) {
+                            const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(x);
+                            b[0] ^= t.x;
+                            b[VW - 1] ^= t.y;
+                        } else {
+                            b[0] ^= x[0];
+                        }
+                    }
                 }
-                *reinterpret_cast<uint64_t*>(&sA[(buf * BM + r) * LD + 2 * w]) = a;
-                *reinterpret_cast<uint64_t*>(&sB[(buf * BN + r) * LD + 2 * w]) = b;
+                uint32_t* da = &sA[(buf * BM + rr[u]) * LD + 2 * ww[u]];
+                uint32_t* db = &sB[(buf * BN + rr[u]) * LD + 2 * ww[u]];
+                if (VW == 2) {
+                    *reinterpret_cast<ulonglong2*>(da) = make_ulonglong2(a[0], a[VW - 1]);
+                    *reinterpret_cast<ulonglong2*>(db) = make_ulonglong2(b[0], b[VW - 1]);
+                } else {
+                    *reinterpret_cast<uint64_t*>(da) = a[0];
+                    *reinterpret_cast<uint64_t*>(db) = b[0];
+                }
             }
         };
 
@@ -314,6 +383,24 @@ __global__ void __launch_bounds__(256, 1)
     }
 }
 
+template <int VW>
+cudaError_t level_attr() {
+    static bool done[MAX_DEVICES] = {false};
+    static cudaError_t err[MAX_DEVICES];
+    static std::mutex mu;
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= MAX_DEVICES)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[d]) {
+        err[d] = cudaFuncSetAttribute(popc_level_kernel<VW>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      LEVEL_SMEM_BYTES);
+        done[d] = true;
+    }
+    return err[d];
+}
+
 }  // namespace
 
 cudaError_t launch_popc_nt(int op, const uint64_t* A, int64_t lda, int64_t strideA,
@@ -346,22 +433,12 @@ cudaError_t launch_popc_level(const uint64_t* A, int64_t lda, int64_t strideA, c
     if (gy > 65535 || count > 65535) return cudaErrorInvalidConfiguration;
     const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)count);
     static_assert(LEVEL_SMEM_BYTES <= 227 * 1024, "fits one CTA's shared memory");
-    {
-        static bool done[MAX_DEVICES] = {false};
-        static cudaError_t err[MAX_DEVICES];
-        static std::mutex mu;
-        int d = 0;
-        if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= MAX_DEVICES)
-            return cudaErrorInvalidDevice;
-        std::lock_guard<std::mutex> lk(mu);
-        if (!done[d]) {
-            err[d] = cudaFuncSetAttribute(popc_level_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          LEVEL_SMEM_BYTES);
-            done[d] = true;
-        }
-        if (err[d] != cudaSuccess) return err[d];
-    }
+    // 16-byte copies where every copied word pair starts 16-byte aligned:
+    // even pitches, even quadrant widths, 16-byte aligned bases and strides
+    const bool wide = hk / 64 % 2 == 0 && lda % 2 == 0 && ldb % 2 == 0 && strideA % 2 == 0 &&
+                      strideB % 2 == 0 && (uintptr_t)A % 16 == 0 && (uintptr_t)Bt % 16 == 0;
+    cudaError_t e = wide ? level_attr<2>() : level_attr<1>();
+    if (e != cudaSuccess) return e;
     // the masks packed into three words: nibble h of xi4 / eta4 = xi[h] /
     // eta[h]; bits 7q..7q+6 of zeta7 = zeta[q]
     uint32_t xi4 = 0, eta4 = 0, zeta7 = 0;
@@ -371,9 +448,12 @@ cudaError_t launch_popc_level(const uint64_t* A, int64_t lda, int64_t strideA, c
     }
     for (int q = 0; q < 4; q++) zeta7 |= (masks.zeta[q] & 0x7Fu) << (7 * q);
     TraceScope ts(BMM_PHASE_BASE, s);
-    popc_level_kernel<<<grid, 256, LEVEL_SMEM_BYTES, s>>>(A, lda, strideA, Bt, ldb, strideB, C,
-                                                          ldc, strideC, hm, hk, hn, xi4, eta4,
-                                                          zeta7);
+    if (wide)
+        popc_level_kernel<2><<<grid, 256, LEVEL_SMEM_BYTES, s>>>(
+            A, lda, strideA, Bt, ldb, strideB, C, ldc, strideC, hm, hk, hn, xi4, eta4, zeta7);
+    else
+        popc_level_kernel<1><<<grid, 256, LEVEL_SMEM_BYTES, s>>>(
+            A, lda, strideA, Bt, ldb, strideB, C, ldc, strideC, hm, hk, hn, xi4, eta4, zeta7);
     return cudaGetLastError();
 }
 

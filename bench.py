@@ -129,7 +129,10 @@ def parse():
     ap.add_argument("--kernel-level", type=int, default=0, choices=[0, 1],
                     help="GF(2): run the innermost Strassen level inside the base-case kernel "
                          "(CUDA-core path)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.kernel_level and args.path != "popc":
+        ap.error("--kernel-level 1 runs on the CUDA-core kernel: add --path popc")
+    return args
 
 
 def peaks():

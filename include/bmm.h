@@ -83,7 +83,8 @@ typedef struct {
     void *workspace;         /* optional device scratch; NULL: stream-ordered allocation */
     uint64_t workspace_bytes;
     int32_t kernel_level;    /* 1: the innermost Strassen level runs inside the base-case
-                                kernel, which forms each of the 7 products' operands from
+                                kernel (a level shifted into the inner layer, Sec. 3.15),
+                                which forms each of the 7 products' operands from
                                 the quadrants as it stages them and folds the products
                                 into the C quadrants in registers (no leaf operands or
                                 leaf products in HBM). Binary product on the CUDA-core

@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(256, 1)
     }
 }
 
-// One Strassen level inside the kernel (the GEMM-side form of a recursion
-// level, Sec. 3.9 with the base case of Sec. 3.10 beneath it): the binary
+// One Strassen level inside the kernel (a level shifted from the expanding
+// and compressing layers into the inner layer, Sec. 3.15): the binary
 // product C (2hm x 2hn) = A (2hm x 2hk) * Bt (2hn x 2hk)^T of one block,
 // through its seven quadrant-sized products. The CTA owns one 128 x 128
 // tile position of the quadrant-sized product and runs the seven products

@@ -49,8 +49,9 @@ bool host_divisible(int64_t m, int64_t k, int64_t n, int d) {
 }
 
 // Device scratch of one product's plan, by the planner's rules (depth from
-// the options or the automatic rule, depth-first levels above two merged
-// ones, k padded for the tensor paths), without asking the device.
+// the options or the automatic rule, the innermost level inside the
+// CUDA-core kernel when asked for, depth-first levels above two merged ones,
+// k padded for the tensor paths), without asking the device.
 uint64_t product_scratch(int op, int64_t m, int64_t k, int64_t n, const bmm_opts& o) {
     int d = 0;
     if (op == OP_GF2) {
@@ -63,10 +64,11 @@ uint64_t product_scratch(int op, int64_t m, int64_t k, int64_t n, const bmm_opts
                 d++;
         }
     }
-    const int serial = d > 2 ? d - 2 : 0;
+    const int od = (o.kernel_level == 1 && d > 0 && o.path == BMM_PATH_POPC) ? d - 1 : d;
+    const int serial = od > 2 ? od - 2 : 0;
     const int64_t unit = (int64_t)128 << d;
     const int64_t kp = o.path == BMM_PATH_POPC ? k : (k + unit - 1) / unit * unit;
-    return workspace_padded(m, k, kp, n, d, serial);
+    return workspace_padded(m, k, kp, n, od, serial);
 }
 
 struct HostPlan {

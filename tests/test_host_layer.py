@@ -59,6 +59,22 @@ def test_plan_auto_takes_the_fewest_levels_that_fit():
     assert bmm.host_plan(bmm.GF2, m, k, n, device_bytes=two)["host_depth"] == 2
 
 
+def test_plan_device_bytes_follow_the_device_plan():
+    """The device estimate is the sub-instance buffers plus the scratch of
+    the device product's own plan, whatever its options: with the innermost
+    level inside the CUDA-core kernel it is the scratch of one level fewer."""
+    built()
+    m = k = n = 16384
+    for d in (1, 2, 3):
+        for kl in (0, 1):
+            kw = dict(path=bmm.PATH_POPC, depth=d, kernel_level=kl)
+            hp = bmm.host_plan(bmm.GF2, m, k, n, device_bytes=1 << 36, host_depth=1, **kw)
+            sm, sk, sn = hp["sub_m"], hp["sub_k"], hp["sub_n"]
+            dev = bmm.plan(bmm.GF2, sm, sk, sn, serial=max(0, d - kl - 2), **kw)
+            bufs = 2 * (sm * sk + sk * sn + sm * sn) // 8
+            assert hp["device_bytes"] == bufs + dev["workspace_bytes"] + (8 << 20)
+
+
 def test_plan_boolean_blocks_c_and_rereads_b_per_block_row():
     built()
     m, k, n = 8192, 4096, 8192

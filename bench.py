@@ -126,6 +126,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="planner rules instead of the autotuner")
+    ap.add_argument("--no-target", action="store_true",
+                    help="skip the m = k = n = 2^19 record (tensor-core and CUDA-core forms, "
+                         "one timed product each) the default workload adds at N = 1")
     ap.add_argument("--kernel-level", type=int, default=0, choices=[0, 1],
                     help="GF(2): run the innermost Strassen level inside the base-case kernel "
                          "(CUDA-core path)")
@@ -537,9 +540,28 @@ def main():
                "ms_per_step": ems / args.steps, **copy_times(torch, upload, download),
                "overlap": OVERLAP}
 
+    # end to end through the library's own host-memory entry points
+    # (bmm_gf2_host / bmm_bool_host): pinned host arrays in and out, each call
+    # blocking until its product is back in host memory
+    e2e_host = None
+    if not args.no_e2e and world == 1:
+        e2e_host = host_api_e2e(torch, bmm, (Ag, Bg, Ab, Bb), m, k, n, args.steps, stream,
+                                kw_g, kw_b)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(n, seed, bool_p)
+
+    # the largest single-GPU configuration, measured in the same run
+    target = None
+    if args.workload == DEFAULT_WORKLOAD and world == 1 and not args.no_target:
+        del Ag, Bg, Ab, Bb, Cg, Cb
+        if e2e is not None:
+            del hA, hC, dA, dC
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        target = target_record(torch, bmm, bitgen, stream, pk, pk_kind,
+                               no_tune=args.no_tune)
 
     if rank == 0:
         line = {
@@ -572,12 +594,133 @@ def main():
             "phases_ms_per_step": {"base": base_ms / args.steps, "xor": xor_ms / args.steps,
                                    "transpose": tr_ms / args.steps},
             "phase_launches": {"base": base_n, "xor": xor_n, "transpose": tr_n},
+            "e2e_host": e2e_host,
+            "target_2pow19": target,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
 
+
+
+def host_api_e2e(torch, bmm, dev_inputs, m, k, n, steps, stream, kw_g, kw_b) -> dict:
+    """The step through bmm_gf2_host / bmm_bool_host: operands and products in
+    pinned host memory, every call uploading its operands, computing and
+    reading its product back before it returns (host wall clock around the
+    calls, which block)."""
+    hAg, hBg, hAb, hBb = (x.cpu().pin_memory() for x in dev_inputs)
+    hCg = torch.empty(m * n // 64, dtype=torch.int64).pin_memory()
+    hCb = torch.empty(m * n // 64, dtype=torch.int64).pin_memory()
+    sh = stream.cuda_stream
+    dev = {key: v for key, v in kw_g.items() if key in ("path", "depth")}
+    devb = {key: v for key, v in kw_b.items() if key == "path"}
+
+    def step():
+        bmm.product_host(bmm.GF2, hAg, hBg, hCg, m, k, n, stream=sh, **dev)
+        bmm.product_host(bmm.BOOL, hAb, hBb, hCb, m, k, n, stream=sh, **devb)
+
+    step()  # warm-up: pinned staging and device buffers are kept between calls
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1000.0
+    pg = bmm.host_plan(bmm.GF2, m, k, n, **dev)
+    pb = bmm.host_plan(bmm.BOOL, m, k, n, **devb)
+    bmm.host_release()
+    return {"value": 2 * (2 * m * k * n) * steps / (ms / 1000.0), "unit": "bop/s",
+            "ms_per_step": ms / steps,
+            "h2d_bytes_per_step": pg["upload_bytes"] + pb["upload_bytes"],
+            "d2h_bytes_per_step": pg["download_bytes"] + pb["download_bytes"],
+            "api": "bmm_gf2_host + bmm_bool_host (pinned host arrays, blocking calls)",
+            "timer": "host wall clock around the blocking calls"}
+
+
+def target_record(torch, bmm, bitgen, stream, pk, pk_kind, no_tune=False) -> dict:
+    """m = k = n = 2^19 (32 GiB per operand; seed 4, GF(2) p = 1/2, Boolean
+    p = 2^-9.5), one product at a time with A, B and C resident in HBM. The
+    tensor-core form (the autotuned path and depth) runs one untimed and one
+    timed product; the CUDA-core form (LOP3/POPC base case, the same Strassen
+    depth for GF(2)) one timed product. Both forms' products are compared
+    word for word on the device."""
+    n, seed, bool_p = WORKLOADS["square524288"]
+    sh = stream.cuda_stream
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    alu_peak = sms * LOP3_LANES_PER_SM_CLK * pk["sm_max_mhz"] * 1e6 * 64 / 1e12
+    out = {"workload": "square524288", "m": n, "k": n, "n": n, "seed": seed,
+           "gf2": "p=1/2", "bool": f"p={bool_p}, cubic",
+           "l2": "inputs larger than L2 (each operand 32 GiB)"}
+    forms = {}
+    for name, op, ids, p in (("gf2", bmm.GF2, IDS_GF2, None), ("bool", bmm.BOOL, IDS_BOOL, bool_p)):
+        if not no_tune:
+            t = bmm.autotune(op, n, n, n, stream=sh)
+            out.setdefault("autotuned", {})[name] = {
+                "path": _path_name(t["path"]), "strassen_depth": t["strassen_depth"],
+                "way": "whole products timed" if t["measured"] else "leaf proxies timed + pass model"}
+        A, B = bmm.empty(n, n), bmm.empty(n, n)
+        bitgen.fill_device(A, n, seed, ids[0], p=p, stream=sh)
+        bitgen.fill_device(B, n, seed, ids[1], p=p, stream=sh)
+        C = bmm.empty(n, n)
+        pt = bmm.plan(op, n, n, n)
+        d = pt["strassen_depth"]
+        flops = 2 * pt["leaves"] * (n >> d) ** 3
+        res = {}
+        for form, kw, warm in (("tensor", {}, True),
+                               ("popcount", {"path": bmm.PATH_POPC, "depth": d}, False)):
+            if form == "popcount":
+                Ct = C
+                C = bmm.empty(n, n)
+            if warm:
+                bmm.product(op, A, B, C, n, n, n, stream=sh, **kw)
+            bmm.stream_status(sh)
+            bmm.trace_enable(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bmm.product(op, A, B, C, n, n, n, stream=sh, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            bmm.trace_enable(False)
+            bmm.stream_status(sh)
+            ms = e0.elapsed_time(e1)
+            _, base_ms = bmm.trace_read(bmm.PHASE_BASE)
+            achieved = flops / (base_ms / 1000.0) / 1e12
+            pl = bmm.plan(op, n, n, n, **kw)
+            if form == "tensor":
+                fp4 = pl["path"] == bmm.PATH_TC_FP4_PAIR
+                peak, src = tensor_peak(pk, pk_kind, fp4)
+                roof = {"bound": "tensor", "achieved": achieved, "peak": peak,
+                        "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src}
+            else:
+                roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak,
+                        "unit": "Tbop/s", "frac": achieved / alu_peak,
+                        "peak_source": f"{sms} SMs x {LOP3_LANES_PER_SM_CLK} LOP3/clk x "
+                                       f"{pk['sm_max_mhz']} MHz x 64 bop"}
+            res[form] = {"product_ms": ms, "bops": 2 * n ** 3 / (ms / 1000.0),
+                         "path": pl["path"], "base_case": _path_name(pl["path"]),
+                         "strassen_depth": pl["strassen_depth"],
+                         "base_ms": base_ms, "roofline": roof,
+                         "timed": "one product" + (" after one untimed" if warm else "")}
+        step = 1 << 28  # words per comparison chunk
+        res["paths_agree"] = all(bool(torch.equal(C[i:i + step], Ct[i:i + step]))
+                                 for i in range(0, C.numel(), step))
+        res["tensor_over_popcount"] = res["popcount"]["product_ms"] / res["tensor"]["product_ms"]
+        forms[name] = res
+        del A, B, C, Ct
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    clocks = sampler.stop()
+    for name in forms:
+        t = forms[name]["tensor"]
+        t["roofline"].update(tensor_pipe(t["roofline"]["achieved"], clocks, pk["sm_max_mhz"],
+                                         t["path"] == bmm.PATH_TC_FP4_PAIR))
+    out["products"] = forms
+    out["clocks"] = clocks
+    return out
 
 
 def batched_problems(count: int, seed: int):
@@ -931,7 +1074,9 @@ def run_batched(args):
 def _path_name(p) -> str:
     return {1: "tcgen05 fp8 (e4m3, f32 accumulate)", 2: "tcgen05 int8 (u8, s32 accumulate)",
             3: "CUDA-core LOP3/POPC",
-            4: "tcgen05 fp8 (e4m3, f32 accumulate), SM pairs (cta_group::2)"}.get(p, str(p))
+            4: "tcgen05 fp8 (e4m3, f32 accumulate), SM pairs (cta_group::2)",
+            5: "tcgen05 fp4 (e2m1, block-scaled kind::mxf4, f32 accumulate), SM pairs "
+               "(cta_group::2)"}.get(p, str(p))
 
 
 if __name__ == "__main__":

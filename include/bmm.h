@@ -297,13 +297,15 @@ bmm_status bmm_basis_change(int32_t variant, int32_t inverse, uint64_t *X, int64
  * Its only scratch, the transpose of B (k x n bits), lives in one static
  * device array of BMM_NOALLOC_SCRATCH_BYTES bytes that every GPU loading
  * this library keeps until the process exits. Sizes with k*n/8 larger than
- * that return BMM_ERR_NOMEM. The first call on each device looks the array's
- * address up (cudaGetSymbolAddress); make that first call before any stream
- * capture begins. All calls share the one array and it keeps the last call's
- * contents; each call writes every word it later reads, so nothing needs
- * clearing, but calls whose work overlaps on the GPU (for example on two
- * streams at once) race on it and must be serialised by the caller. With
- * tracing on (bmm_trace_enable), launches also create CUDA events. */
+ * that return BMM_ERR_NOMEM. Every call looks the array's device address up
+ * (cudaGetSymbolAddress, with the calling device current); the first call
+ * on a device also loads this library's device code there, so make that
+ * first call before any stream capture begins. All calls share the one
+ * array and it keeps the last call's contents; each call writes every word
+ * it later reads, so nothing needs clearing, but calls whose work overlaps
+ * on the GPU (for example on two streams at once) race on it and must be
+ * serialised by the caller. With tracing on (bmm_trace_enable), launches
+ * also create CUDA events. */
 bmm_status bmm_product_noalloc(int32_t op, const uint64_t *A, const uint64_t *B, uint64_t *C,
                                int64_t m, int64_t k, int64_t n, bmm_stream_t stream);
 

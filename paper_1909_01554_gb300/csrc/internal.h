@@ -25,6 +25,11 @@ bmm_status cuda_fail(cudaError_t e);
         if (bmm_e_ != cudaSuccess) return cuda_fail(bmm_e_); \
     } while (0)
 
+// The argument checks every product entry point shares: null pointers,
+// sizes (positive multiples of 64), 16-byte alignment, C overlapping A or B.
+bmm_status check_product_args(const uint64_t* A, const uint64_t* B, const uint64_t* C,
+                              int64_t m, int64_t k, int64_t n);
+
 // Tracing hooks: wrap every kernel launch in a TraceScope.
 void trace_launch_begin(int phase, cudaStream_t s, void** token);
 void trace_launch_end(void* token, cudaStream_t s);

@@ -6,8 +6,6 @@ with probability <= 1/2).
 
 Inputs on the GPU come from the device generator; the oracle's inputs come
 from the CPU generator (the two are checked equal in test_gpu_parity)."""
-import os
-
 import numpy as np
 import pytest
 
@@ -131,12 +129,11 @@ def test_config3_square65536_paths_agree():
         sampled_check(op, n, seed, ids, p, tc, nrows=4, ncols=4, freivalds=4)
 
 
-@pytest.mark.skipif(os.environ.get("BMM_TEST_2POW19") != "1",
-                    reason="m = k = n = 2^19 (32 GiB per operand, minutes): set BMM_TEST_2POW19=1")
 def test_config4_square524288():
-    """m = k = n = 2^19, seed 4: GF(2) p = 1/2 through the planner's Strassen
-    (depth-first top levels so that it fits HBM), Boolean p = 2^-9.5 cubic;
-    sampled rows and columns plus GF(2) Freivalds."""
+    """m = k = n = 2^19 (32 GiB per operand, minutes), seed 4: GF(2) p = 1/2
+    through the planner's Strassen (depth-first top levels so that it fits
+    HBM), Boolean p = 2^-9.5 cubic; sampled rows and columns plus GF(2)
+    Freivalds."""
     n, seed = 1 << 19, 4
     Cg = run_product(bmm.GF2, n, seed, IDS_GF2, None)
     sampled_check(bmm.GF2, n, seed, IDS_GF2, None, Cg, nrows=4, ncols=4, freivalds=4)

@@ -218,13 +218,39 @@ def test_strassen_variants(variant, depth, serial):
     check(got, want, f"strassen v={variant} d={depth} s={serial}")
 
 
-# The innermost level inside the CUDA-core kernel. m, k, n = (320, 576, 448)
-# << depth: the in-kernel quadrants are 2.5 x 3.5 tiles of 128 and 9 words of
-# k (two full stages of 4 and a ragged one).
+# The Strassen passes over the tensor-core base cases. Shapes (mq, kq, nq) <<
+# depth give leaves of mq x kq x nq bits: 320 and 384 leaf rows are not
+# multiples of the 256-row SM-pair tile, and kq = 192 is not a multiple of the
+# 128 bits a tensor leaf needs, so the plan pads k (zero columns of A, zero
+# rows of B) below every level.
+@pytest.mark.parametrize("path,shape", [(bmm.PATH_TC_FP4_PAIR, (320, 192, 448)),
+                                        (bmm.PATH_TC_FP4_PAIR, (384, 256, 320)),
+                                        (bmm.PATH_TC_FP8_PAIR, (320, 192, 448))])
+@pytest.mark.parametrize("variant", [bmm.WINOGRAD, bmm.SELF_INVERSE, bmm.CHAINING])
+@pytest.mark.parametrize("depth,serial", [(1, 0), (2, 0), (1, 1), (2, 1), (3, 1), (3, 2)])
+def test_strassen_variants_tensor(path, shape, variant, depth, serial):
+    if not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    m, k, n = (x << depth for x in shape)
+    info = bmm.plan(bmm.GF2, m, k, n, depth=depth, serial=serial, variant=variant, path=path)
+    assert info["path"] == path and info["serial_depth"] == serial
+    Ah, Bh = gen(m, k, 41, 0), gen(k, n, 41, 1)
+    want = O.cubic(O.GF2, Ah, Bh, m, k, n)
+    got = run(bmm.GF2, Ah, Bh, m, k, n, depth=depth, serial=serial, variant=variant, path=path)
+    check(got, want, f"strassen path={path} {shape} v={variant} d={depth} s={serial}")
+
+
+# The innermost level inside the CUDA-core kernel. m, k, n = (320, kq, 448)
+# << depth: the in-kernel quadrants are 2.5 x 3.5 tiles of 128 rows and
+# kq = 576 bits (9 words of k: two full stages of 4 and a ragged one; 8-byte
+# copies) or kq = 512 bits (8 words; every pitch and stride the launcher sees
+# is then a multiple of 8 words too, so it takes the 16-byte copy form, here
+# on the same ragged row tiles).
+@pytest.mark.parametrize("kq", [576, 512])
 @pytest.mark.parametrize("variant", [bmm.WINOGRAD, bmm.SELF_INVERSE, bmm.CHAINING])
 @pytest.mark.parametrize("depth,serial", [(1, 0), (2, 0), (2, 1), (3, 1), (3, 2)])
-def test_kernel_level(variant, depth, serial):
-    m, k, n = 320 << depth, 576 << depth, 448 << depth
+def test_kernel_level(variant, depth, serial, kq):
+    m, k, n = 320 << depth, kq << depth, 448 << depth
     Ah, Bh = gen(m, k, 29, 0), gen(k, n, 29, 1)
     want = O.cubic(O.GF2, Ah, Bh, m, k, n)
     info = bmm.plan(bmm.GF2, m, k, n, depth=depth, serial=serial, variant=variant,

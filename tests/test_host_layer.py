@@ -73,6 +73,11 @@ def test_plan_device_bytes_follow_the_device_plan():
             dev = bmm.plan(bmm.GF2, sm, sk, sn, serial=max(0, d - kl - 2), **kw)
             bufs = 2 * (sm * sk + sk * sn + sm * sn) // 8
             assert hp["device_bytes"] == bufs + dev["workspace_bytes"] + (8 << 20)
+            if not bmm.device_supported():
+                # AUTO resolves to the CUDA cores here: the same estimate
+                auto = dict(kw, path=bmm.PATH_AUTO)
+                ha = bmm.host_plan(bmm.GF2, m, k, n, device_bytes=1 << 36, host_depth=1, **auto)
+                assert ha["device_bytes"] == hp["device_bytes"]
 
 
 def test_plan_boolean_blocks_c_and_rereads_b_per_block_row():

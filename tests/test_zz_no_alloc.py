@@ -1,16 +1,18 @@
-"""The allocation-free product (bmm_product_noalloc) against bmm_gf2 / bmm_bool.
+"""The allocation-free product (bmm_product_noalloc) against the CPU oracle
+and against bmm_gf2 / bmm_bool.
 
 It serves callers that cannot allocate device memory while they run; its
 only scratch is a fixed device array shared by every call. Two calls in a row
-with different inputs must each match the allocating entry points bit for
-bit (so nothing left in the array from the first call leaks into the second),
-and sizes beyond the array are refused. This file is named to be collected
-last, and passes both alone in a fresh process and after the other tests."""
+with different inputs must each match the oracle's product and the
+allocating entry point's bit for bit (so nothing left in the array from the
+first call leaks into the second), and sizes beyond the array are refused.
+This file is named to be collected last, and passes both alone in a fresh
+process and after the other tests."""
 import ctypes
 
-import numpy as np
 import pytest
 
+import oracle as O
 from gpu_util import first_mismatch, from_dev, gen, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -30,18 +32,22 @@ def noalloc(op, dA, dB, dC, m, k, n):
 
 
 @pytest.mark.parametrize("op", [bmm.GF2, bmm.BOOL])
-def test_noalloc_matches_allocating_entry_point_twice(op):
+def test_noalloc_matches_oracle_and_allocating_entry_point_twice(op):
     shapes = [(1024, 2048, 1536, 31), (448, 1344, 960, 32)]  # second call: ragged, smaller
     for m, k, n, seed in shapes:
         p = None if op == bmm.GF2 else "1/32"
-        dA, dB = to_dev(gen(m, k, seed, 0, p)), to_dev(gen(k, n, seed, 1, p))
+        Ah, Bh = gen(m, k, seed, 0, p), gen(k, n, seed, 1, p)
+        want = O.cubic(O.GF2 if op == bmm.GF2 else O.BOOL, Ah, Bh, m, k, n)
+        dA, dB = to_dev(Ah), to_dev(Bh)
         ref, got = bmm.empty(m, n), bmm.empty(m, n)
         got.fill_(-1)
         bmm.product(op, dA, dB, ref, m, k, n)
         assert noalloc(op, dA, dB, got, m, k, n) == bmm.OK
         bmm.stream_status()
+        mm = first_mismatch(from_dev(got, m, n), want)
+        assert mm is None, f"op={op} shape={(m, k, n)} against the oracle: {mm}"
         mm = first_mismatch(from_dev(got, m, n), from_dev(ref, m, n))
-        assert mm is None, f"op={op} shape={(m, k, n)}: {mm}"
+        assert mm is None, f"op={op} shape={(m, k, n)} against bmm_gf2/bmm_bool: {mm}"
 
 
 def test_noalloc_refuses_sizes_beyond_its_scratch():

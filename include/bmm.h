@@ -177,28 +177,95 @@ bmm_status bmm_bool_batched(int32_t count, const uint64_t *const *A, const uint6
                             uint64_t *const *C, const int64_t *m, const int64_t *k,
                             const int64_t *n, bmm_stream_t stream);
 
-/* Reusable batch plan. create builds, on the current device: TMA maps per
- * problem, the tile work list and its assignment to SMs (longest first onto
- * the least loaded SM), and scratch for the transposed B's; it allocates
- * device memory and copies to it synchronously. run launches three kernels on
- * `stream` (batched transpose, row padding for k/64 odd, persistent base
- * case), allocates nothing and does not synchronise; it reads the matrices
- * named at create time, so new data in the same buffers needs no new plan.
- * destroy frees the plan; call it only after the runs have completed. */
+/* Reusable batch plan. create decides, per problem, its base case (the
+ * tensor cores or the CUDA cores) and its tile form (a last column tile of
+ * N = 128 where at most 128 of its 256 columns lie inside n; k in operand
+ * stages of 256 bits for e2m1, 128 for e4m3, so half a packed stage at the
+ * end is not multiplied) from a cost model measured on the device: per
+ * stage of k and per tile of each kernel, from synthetic batches timed the
+ * first time a plan on that device and tensor path needs it (Sec. 3.17:
+ * what memory does not fix is chosen by measurement; that first create
+ * takes some tens of milliseconds longer). Every problem runs cubic
+ * (Strassen depth 0): the planner's depth rule keeps leaves of at least
+ * 8192 bits, so it gives depth 0 to every side below 16384, and a batch
+ * plan has no XOR passes. It then builds, on the current device, TMA maps
+ * per problem, the tensor tile work list and its assignment to SM pairs
+ * (longest first onto the least loaded pair, by model cost), the CUDA-core
+ * tile list, and scratch for the transposed B's; it allocates device memory
+ * and copies to it synchronously. run launches on `stream` a batched
+ * transpose, row padding for tensor problems with k/64 odd, one persistent
+ * tensor-core launch and, when some problem chose the CUDA cores, one
+ * persistent CUDA-core launch; it allocates nothing and does not
+ * synchronise, and it reads the matrices named at create time, so new data
+ * in the same buffers needs no new plan. destroy frees the plan; call it
+ * only after the runs have completed. */
 typedef struct bmm_batched_plan_s *bmm_batched_plan;
 bmm_status bmm_batched_plan_create(int32_t count, const int32_t *op, const uint64_t *const *A,
                                    const uint64_t *const *B, uint64_t *const *C, const int64_t *m,
                                    const int64_t *k, const int64_t *n, bmm_batched_plan *plan);
-/* As create, every problem on base-case `path` (bmm_path; AUTO as create;
- * an explicit tensor path the device lacks: BMM_ERR_UNSUPPORTED). */
+/* As create, every problem on base-case `path` (bmm_path; AUTO as create,
+ * the model choosing per problem; an explicit tensor path the device lacks:
+ * BMM_ERR_UNSUPPORTED; tail tile forms still follow the model). */
 bmm_status bmm_batched_plan_create_ex(int32_t count, const int32_t *op, const uint64_t *const *A,
                                       const uint64_t *const *B, uint64_t *const *C,
                                       const int64_t *m, const int64_t *k, const int64_t *n,
                                       int32_t path, bmm_batched_plan *plan);
 bmm_status bmm_batched_plan_run(bmm_batched_plan plan, bmm_stream_t stream);
 bmm_status bmm_batched_plan_destroy(bmm_batched_plan plan);
-/* The base-case path (bmm_path, never AUTO) the plan runs. */
+/* As create with the base case named per problem: paths[i] is
+ * BMM_PATH_AUTO (the model chooses), BMM_PATH_POPC, or a tensor path; every
+ * tensor entry must name the same tensor path (else BMM_ERR_INVALID), and
+ * AUTO entries choose between it (or, if none is named, the device's
+ * automatic tensor path) and the CUDA cores. paths is host memory. */
+bmm_status bmm_batched_plan_create_paths(int32_t count, const int32_t *op,
+                                         const uint64_t *const *A, const uint64_t *const *B,
+                                         uint64_t *const *C, const int64_t *m, const int64_t *k,
+                                         const int64_t *n, const int32_t *paths,
+                                         bmm_batched_plan *plan);
+/* The plan's tensor path (bmm_path, never AUTO) if any problem runs on the
+ * tensor cores, else BMM_PATH_POPC. */
 bmm_status bmm_batched_plan_path(bmm_batched_plan plan, int32_t *path);
+
+/* What a plan decided for problem i (0 <= i < count). */
+typedef struct {
+    int32_t path;           /* base case: a tensor path or BMM_PATH_POPC */
+    int32_t tile_m, tile_n; /* rows and columns of C per tile */
+    int32_t tail_n;         /* columns the MMAs of its last column tile cover (tile_n or 128) */
+    int32_t k_step;         /* bits of k per step the tiles run in (k is padded to whole steps) */
+    int64_t k_steps;        /* steps of k per tile */
+    int32_t strassen_depth; /* 0: batched problems run cubic */
+    double est_us;          /* the model's time for all its tiles on one unit (CTA pair or CTA) */
+} bmm_batched_choice;
+bmm_status bmm_batched_plan_choice(bmm_batched_plan plan, int32_t i, bmm_batched_choice *out);
+
+/* Totals of a plan. macs_issued / macs_needed is the padding the tiles
+ * carry (MACs computed over sum of m k n). */
+typedef struct {
+    int32_t problems, tensor_problems, popc_problems;
+    int32_t tensor_path;          /* the tensor path the plan uses for tensor problems */
+    int64_t tensor_tiles, tensor_tiles_n128, popc_tiles;
+    double macs_needed, macs_issued;
+    double est_ms;                /* the model's base-case time of one run */
+    int32_t model_measured;       /* 1: the model was measured on this device */
+} bmm_batched_stats;
+bmm_status bmm_batched_plan_stats(bmm_batched_plan plan, bmm_batched_stats *out);
+
+/* The batched cost model for a tensor path (AUTO: the device's automatic
+ * one; BMM_PATH_POPC: the CUDA-core part only) on the current device,
+ * measured now if it was not yet (synchronises the device). Times are
+ * nanoseconds on one unit of the launch. */
+typedef struct {
+    int32_t path;
+    int32_t measured;
+    int32_t tensor_units;          /* CTA pairs (or CTAs) of the tensor launch */
+    double tensor_stage_ns;        /* per operand stage of an N = 256 tile */
+    double tensor_stage_n128_ns;   /* per operand stage of an N = 128 tile */
+    double tensor_tile_ns;         /* per tile */
+    int32_t popc_units;            /* CTAs of the CUDA-core launch */
+    double popc_stage_ns;          /* per 256-bit stage of k of a 128 x 128 tile */
+    double popc_tile_ns;           /* per tile */
+} bmm_batched_model_info;
+bmm_status bmm_batched_model(int32_t path, bmm_batched_model_info *out);
 
 /* ---- operands in host memory: the host layer (Secs. 3.12-3.14, Alg. 3) ---
  *

@@ -31,7 +31,8 @@ EXPORTED = [
     "bmm_trace_enable", "bmm_trace_read", "bmm_launch_count", "bmm_autotune",
     "bmm_autotune_clear", "bmm_batched_plan_path", "bmm_batched_plan_create_ex",
     "bmm_host_opts_default", "bmm_host_plan", "bmm_gf2_host", "bmm_bool_host",
-    "bmm_host_release",
+    "bmm_host_release", "bmm_batched_plan_create_paths", "bmm_batched_plan_choice",
+    "bmm_batched_plan_stats", "bmm_batched_model",
 ]
 TUNE_MODEL = 1
 PHASE_BASE, PHASE_XOR, PHASE_TRANSPOSE = 0, 1, 2
@@ -78,6 +79,30 @@ class PlanInfo(ctypes.Structure):
                 ("kernel_level", ctypes.c_int32)]
 
 
+class BatchedChoice(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("tile_m", ctypes.c_int32), ("tile_n", ctypes.c_int32),
+                ("tail_n", ctypes.c_int32), ("k_step", ctypes.c_int32),
+                ("k_steps", ctypes.c_int64), ("strassen_depth", ctypes.c_int32),
+                ("est_us", ctypes.c_double)]
+
+
+class BatchedStats(ctypes.Structure):
+    _fields_ = [("problems", ctypes.c_int32), ("tensor_problems", ctypes.c_int32),
+                ("popc_problems", ctypes.c_int32), ("tensor_path", ctypes.c_int32),
+                ("tensor_tiles", ctypes.c_int64), ("tensor_tiles_n128", ctypes.c_int64),
+                ("popc_tiles", ctypes.c_int64), ("macs_needed", ctypes.c_double),
+                ("macs_issued", ctypes.c_double), ("est_ms", ctypes.c_double),
+                ("model_measured", ctypes.c_int32)]
+
+
+class BatchedModel(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("measured", ctypes.c_int32),
+                ("tensor_units", ctypes.c_int32), ("tensor_stage_ns", ctypes.c_double),
+                ("tensor_stage_n128_ns", ctypes.c_double), ("tensor_tile_ns", ctypes.c_double),
+                ("popc_units", ctypes.c_int32), ("popc_stage_ns", ctypes.c_double),
+                ("popc_tile_ns", ctypes.c_double)]
+
+
 _LIB = None
 
 
@@ -116,6 +141,15 @@ def _lib_handle():
         L.bmm_batched_plan_destroy.restype = i32
         L.bmm_batched_plan_path.argtypes = [vp, ctypes.POINTER(i32)]
         L.bmm_batched_plan_path.restype = i32
+        L.bmm_batched_plan_create_paths.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp,
+                                                    ctypes.POINTER(ctypes.c_void_p)]
+        L.bmm_batched_plan_create_paths.restype = i32
+        L.bmm_batched_plan_choice.argtypes = [vp, i32, ctypes.POINTER(BatchedChoice)]
+        L.bmm_batched_plan_choice.restype = i32
+        L.bmm_batched_plan_stats.argtypes = [vp, ctypes.POINTER(BatchedStats)]
+        L.bmm_batched_plan_stats.restype = i32
+        L.bmm_batched_model.argtypes = [i32, ctypes.POINTER(BatchedModel)]
+        L.bmm_batched_model.restype = i32
         L.bmm_transpose.argtypes = [vp, vp, i64, i64, vp]
         L.bmm_transpose.restype = i32
         L.bmm_base_product.argtypes = [i32, i32, vp, vp, vp, i64, i64, i64, vp]
@@ -353,18 +387,44 @@ def batched(ops, As, Bs, Cs, ms, ks, ns, stream=None) -> None:
     _check(_lib_handle().bmm_batched(*arr, _stream(stream)), "bmm_batched")
 
 
+def _struct_dict(x) -> dict:
+    return {f: getattr(x, f) for f, _ in x._fields_}
+
+
 class BatchedPlan:
     """A reusable batch plan (see bmm_batched_plan_create); run() only launches.
-    path: a bmm_path for every problem (default: the automatic choice)."""
+    path: a bmm_path for every problem (default: the automatic choice per
+    problem); paths: one bmm_path per problem instead (AUTO entries left to
+    the model)."""
 
-    def __init__(self, ops, As, Bs, Cs, ms, ks, ns, path: int = PATH_AUTO):
+    def __init__(self, ops, As, Bs, Cs, ms, ks, ns, path: int = PATH_AUTO, paths=None):
         if isinstance(ops, int):
             ops = [ops] * len(As)
         self._arr = _batch_arrays(ops, As, Bs, Cs, ms, ks, ns)
         h = ctypes.c_void_p(0)
-        _check(_lib_handle().bmm_batched_plan_create_ex(*self._arr, path, ctypes.byref(h)),
-               "bmm_batched_plan_create_ex")
+        if paths is None:
+            _check(_lib_handle().bmm_batched_plan_create_ex(*self._arr, path, ctypes.byref(h)),
+                   "bmm_batched_plan_create_ex")
+        else:
+            self._paths = (ctypes.c_int32 * len(paths))(*paths)
+            _check(_lib_handle().bmm_batched_plan_create_paths(*self._arr, self._paths,
+                                                               ctypes.byref(h)),
+                   "bmm_batched_plan_create_paths")
         self._h = h
+
+    def choice(self, i: int) -> dict:
+        """What the plan decided for problem i (path, tile form, k steps)."""
+        c = BatchedChoice()
+        _check(_lib_handle().bmm_batched_plan_choice(self._h, i, ctypes.byref(c)),
+               "bmm_batched_plan_choice")
+        return _struct_dict(c)
+
+    def stats(self) -> dict:
+        """Problems per path, tiles per form, MACs needed and issued, model time."""
+        st = BatchedStats()
+        _check(_lib_handle().bmm_batched_plan_stats(self._h, ctypes.byref(st)),
+               "bmm_batched_plan_stats")
+        return _struct_dict(st)
 
     def run(self, stream=None) -> None:
         _check(_lib_handle().bmm_batched_plan_run(self._h, _stream(stream)),
@@ -387,6 +447,14 @@ class BatchedPlan:
             self.destroy()
         except Exception:
             pass
+
+
+def batched_model(path: int = PATH_AUTO) -> dict:
+    """The batched schedule's cost model on the current device (measured on
+    first use)."""
+    m = BatchedModel()
+    _check(_lib_handle().bmm_batched_model(path, ctypes.byref(m)), "bmm_batched_model")
+    return _struct_dict(m)
 
 
 def stream_status(stream=None) -> None:

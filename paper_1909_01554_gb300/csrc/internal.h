@@ -85,6 +85,26 @@ cudaError_t launch_popc_nt(int op, const uint64_t* A, int64_t lda, int64_t strid
                            int64_t ldc, int64_t strideC, int64_t count, int64_t m, int64_t k,
                            int64_t n, cudaStream_t s);
 
+// Batched CUDA-core base case: one problem C (m x n, pitch ldc) = A (m x k,
+// pitch lda) times Bt^T (Bt n x k, pitch ldb), and one 128 x 128 tile of it.
+struct PopcJob {
+    const uint64_t* A;
+    const uint64_t* Bt;
+    uint64_t* C;
+    int64_t lda, ldb, ldc, m, k, n;
+    int32_t op, pad;
+};
+struct PopcTile {
+    int32_t job, tm, tn, pad;
+};
+constexpr int POPC_TILE = 128;
+// Every tile of the (device) list in one persistent launch; the list is
+// walked in order, CTA b taking tiles b, b + grid, ...
+cudaError_t launch_popc_batched(const PopcJob* jobs, const PopcTile* tiles, int64_t count,
+                                cudaStream_t s);
+// CTAs of that launch (resident blocks per SM x SMs).
+int popc_batched_grid();
+
 // Combined standard-basis operators of one Strassen level as 0/1 masks:
 // xi[h] bit q = block q of A enters product h, eta[h] likewise for B,
 // zeta[q] bit h = product h enters block q of C (blocks q = 2*row + col).

@@ -16,6 +16,7 @@
 // loads of 16 bytes. Rows are padded to 48 bytes, which keeps every
 // quarter-warp's 128-bit loads on distinct banks. The epilogue gathers the
 // result bits of a warp with ballots and writes whole 64-bit words.
+#include <algorithm>
 #include <mutex>
 
 #include "internal.h"
@@ -117,21 +118,18 @@ __device__ __forceinline__ uint64_t tile_word(const uint32_t (&acc)[8][8], int l
     return myword;
 }
 
+// One 128 x 128 tile of C (rows row0.., columns col0..) = A * Bt^T over the
+// whole of k: the cp.async ring, the LOP3 loop and the ballot epilogue.
 template <int OP>
-__global__ void __launch_bounds__(256, 1)
-    popc_nt_kernel(const uint64_t* __restrict__ A, int64_t lda, int64_t strideA,
-                   const uint64_t* __restrict__ Bt, int64_t ldb, int64_t strideB,
-                   uint64_t* __restrict__ C, int64_t ldc, int64_t strideC, int64_t m, int64_t k,
-                   int64_t n) {
-    A += (int64_t)blockIdx.z * strideA;
-    Bt += (int64_t)blockIdx.z * strideB;
-    C += (int64_t)blockIdx.z * strideC;
-    extern __shared__ __align__(16) uint32_t smem[];
+__device__ __forceinline__ void popc_tile(const uint64_t* __restrict__ A, int64_t lda,
+                                          const uint64_t* __restrict__ Bt, int64_t ldb,
+                                          uint64_t* __restrict__ C, int64_t ldc, int64_t m,
+                                          int64_t k, int64_t n, int64_t row0, int64_t col0,
+                                          uint32_t* smem) {
     uint32_t* sA = smem;                      // [STAGES][BM][LD]
     uint32_t* sB = smem + STAGES * BM * LD;   // [STAGES][BN][LD]
 
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t row0 = (int64_t)blockIdx.y * BM, col0 = (int64_t)blockIdx.x * BN;
     const int64_t kwords = k / 64;
     const int nk = (int)((kwords + KW64 - 1) / KW64);
 
@@ -186,6 +184,38 @@ __global__ void __launch_bounds__(256, 1)
         const int64_t row = row0 + 2 * warp + half + 16 * i;
         const int64_t cw = col0 / 64 + w;
         if (row < m && cw < n / 64) C[row * ldc + cw] = myword;
+    }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(256, 1)
+    popc_nt_kernel(const uint64_t* __restrict__ A, int64_t lda, int64_t strideA,
+                   const uint64_t* __restrict__ Bt, int64_t ldb, int64_t strideB,
+                   uint64_t* __restrict__ C, int64_t ldc, int64_t strideC, int64_t m, int64_t k,
+                   int64_t n) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    popc_tile<OP>(A + (int64_t)blockIdx.z * strideA, lda, Bt + (int64_t)blockIdx.z * strideB, ldb,
+                  C + (int64_t)blockIdx.z * strideC, ldc, m, k, n, (int64_t)blockIdx.y * BM,
+                  (int64_t)blockIdx.x * BN, smem);
+}
+
+// Products of uneven sizes in one persistent launch: CTA b takes tiles b,
+// b + gridDim.x, ... of the list (ordered longest first by the planner), each
+// a 128 x 128 tile of one problem's C over that problem's whole k.
+__global__ void __launch_bounds__(256, 1)
+    popc_batched_kernel(const PopcJob* __restrict__ jobs, const PopcTile* __restrict__ tiles,
+                        int64_t count) {
+    extern __shared__ __align__(16) uint32_t smem[];
+    for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
+        const PopcTile w = tiles[t];
+        const PopcJob j = jobs[w.job];
+        __syncthreads();  // the previous tile's last stage has been read by every thread
+        if (j.op == OP_GF2)
+            popc_tile<OP_GF2>(j.A, j.lda, j.Bt, j.ldb, j.C, j.ldc, j.m, j.k, j.n,
+                              (int64_t)w.tm * BM, (int64_t)w.tn * BN, smem);
+        else
+            popc_tile<OP_BOOL>(j.A, j.lda, j.Bt, j.ldb, j.C, j.ldc, j.m, j.k, j.n,
+                               (int64_t)w.tm * BM, (int64_t)w.tn * BN, smem);
     }
 }
 
@@ -419,6 +449,34 @@ cudaError_t launch_popc_nt(int op, const uint64_t* A, int64_t lda, int64_t strid
     else
         popc_nt_kernel<OP_BOOL><<<grid, 256, SMEM_BYTES, s>>>(A, lda, strideA, Bt, ldb, strideB,
                                                               C, ldc, strideC, m, k, n);
+    return cudaGetLastError();
+}
+
+int popc_batched_grid() {
+    static int grid[MAX_DEVICES] = {0};
+    static std::mutex mu;
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= MAX_DEVICES) return sm_count();
+    std::lock_guard<std::mutex> lk(mu);
+    if (!grid[d]) {
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, popc_batched_kernel, 256,
+                                                          SMEM_BYTES) != cudaSuccess ||
+            per < 1) {
+            (void)cudaGetLastError();
+            per = 1;
+        }
+        grid[d] = per * sm_count();
+    }
+    return grid[d];
+}
+
+cudaError_t launch_popc_batched(const PopcJob* jobs, const PopcTile* tiles, int64_t count,
+                                cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int64_t g = std::min<int64_t>(count, popc_batched_grid());
+    TraceScope ts(BMM_PHASE_BASE, s);
+    popc_batched_kernel<<<(unsigned)g, 256, SMEM_BYTES, s>>>(jobs, tiles, count);
     return cudaGetLastError();
 }
 

@@ -16,13 +16,17 @@ struct TcProblem {
     CUtensorMap mapB;  // Bt (n x k)
     uint64_t* C;
     int64_t ldc;       // words
-    int32_t m, n, nks, op;  // nks: k stages (128 bits e4m3, 256 bits e2m1), a multiple of 2
+    int32_t m, n, nks, op;  // nks: k stages (128 bits e4m3, 256 bits e2m1)
 };
 
 // One output tile (TC_TILE_M rows, or 2 * TC_TILE_M for an SM pair, x
 // TC_TILE_N columns) of one problem; tm counts tiles of that height.
 struct TcWorkItem {
-    int32_t prob, tm, tn, nks;  // nks: the problem's k stages (read without the problem table)
+    int32_t prob, tm, tn;
+    int32_t nks;   // the problem's k stages (read without the problem table); may be odd:
+                   // the last packed stage then runs only its first operand stage's MMAs
+    int32_t n128;  // 1: the tile's MMAs are N = 128 (its columns past 128 lie beyond n)
+    int32_t pad[3];
 };
 
 constexpr int TC_TILE_M = 128;

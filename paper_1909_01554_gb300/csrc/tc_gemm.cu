@@ -284,18 +284,18 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
 
 // Instruction descriptor for kind::f8f6f4: D format (1 = F32), A and B
 // format 0 (E4M3), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-template <int M>
+template <int M, int N = BN>
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t dfmt) {
-    return (dfmt << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    return (dfmt << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // Instruction descriptor for kind::mxf4 (block-scaled e2m1, FP32
 // accumulate): A and B format 1 (E2M1) at bits 7 and 10, both K-major,
 // N >> 3 at bit 17, scale format 1 (UE8M0) at bit 23, M >> 4 at bit 24;
 // scale-factor data ids 0 and K = 64 (bit 31 clear).
-template <int M>
+template <int M, int N = BN>
 __host__ __device__ constexpr uint32_t instr_desc_mxf4() {
-    return (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | (1u << 23) |
+    return (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | (1u << 23) |
            ((uint32_t)(M >> 4) << 24);
 }
 
@@ -536,6 +536,7 @@ struct Tile {
     uint64_t* C;  // leaf's C
     int64_t ldc;
     int m, n, nks, op, tm, tn, leaf;
+    int n128;     // batched: N = 128 MMAs (columns 128.. of the tile lie past n)
 };
 
 // Scheduling unit: a CTA, or a CTA pair (consecutive blockIdx.x, one cluster).
@@ -570,11 +571,12 @@ __device__ __forceinline__ Tile tile_get(const Params& p, int idx, const CUtenso
         t.ldc = d->ldc;
         t.m = d->m;
         t.n = d->n;
-        t.nks = d->nks;
+        t.nks = w.nks;
         t.op = d->op;
         t.tm = w.tm;
         t.tn = w.tn;
         t.leaf = 0;
+        t.n128 = w.n128;
     } else {
         const TileCoord c =
             tile_of(unit_id<PAIR>() + idx * unit_count<PAIR>(), p.tiles_m, p.tiles_n);
@@ -589,14 +591,26 @@ __device__ __forceinline__ Tile tile_get(const Params& p, int idx, const CUtenso
         t.tm = c.tm;
         t.tn = c.tn;
         t.leaf = c.leaf;
+        t.n128 = 0;
     }
     return t;
 }
 
+// What the MMA issuer needs of a tile: its k stages, and (batched) N = 128.
+struct TileK {
+    int nks, n128;
+};
 template <bool BATCHED, bool PAIR>
-__device__ __forceinline__ int tile_nks(const Params& p, int idx) {
-    if (BATCHED) return p.items[p.cta_ptr[unit_id<PAIR>()] + idx].nks;
-    return p.nks;
+__device__ __forceinline__ TileK tile_k(const Params& p, int idx) {
+    if (BATCHED) {
+        const TcWorkItem* w = p.items + p.cta_ptr[unit_id<PAIR>()] + idx;
+        return {w->nks, w->n128};
+    }
+    return {p.nks, 0};
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* m) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
 }
 
 template <bool BATCHED, bool PAIR, bool FP4>
@@ -672,11 +686,28 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) {
             int pit = 0;  // packed stages issued
             bool ok = true;
+            // Batched: a tile's work item is read two tiles ahead and its
+            // TMA maps prefetched one tile ahead, so neither the item load
+            // nor a map fetch stalls the copies of the tile before it.
+            Tile nxt = my_tiles > 0 ? tile_get<BATCHED, PAIR>(p, 0, &tmA, &tmB) : Tile{};
+            Tile nxt2 = my_tiles > 1 ? tile_get<BATCHED, PAIR>(p, 1, &tmA, &tmB) : nxt;
+            if (BATCHED && my_tiles > 0) {
+                prefetch_tensormap(nxt.ma);
+                prefetch_tensormap(nxt.mb);
+            }
             for (int i = 0; ok && i < my_tiles; i++) {
-                const Tile tc = tile_get<BATCHED, PAIR>(p, i, &tmA, &tmB);
+                const Tile tc = nxt;
+                nxt = nxt2;
+                if (BATCHED && i + 1 < my_tiles) {
+                    prefetch_tensormap(nxt.ma);
+                    prefetch_tensormap(nxt.mb);
+                }
+                if (i + 2 < my_tiles) nxt2 = tile_get<BATCHED, PAIR>(p, i + 2, &tmA, &tmB);
                 const int arow = tc.tm * LY::TILE_M + (int)rank * BM;
-                const int brow = tc.tn * BN + (int)rank * LY::BROWS;
-                for (int kp = 0; kp < tc.nks / SUB; kp++, pit++) {
+                // an N = 128 tile takes 64 of its columns from each CTA of a pair
+                const int brow =
+                    tc.tn * BN + (int)rank * (BATCHED && tc.n128 ? LY::BROWS / 2 : LY::BROWS);
+                for (int kp = 0; kp < (tc.nks + SUB - 1) / SUB; kp++, pit++) {
                     const int s = pit % PSTAGES;
                     if (!mbar_wait(empty_p(s), ((pit / PSTAGES) & 1) ^ 1, p.err)) {
                         ok = false;
@@ -830,6 +861,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0 && rank == 0) {
             constexpr uint32_t idesc =
                 FP4 ? instr_desc_mxf4<LY::TILE_M>() : instr_desc<LY::TILE_M>(1u);
+            constexpr uint32_t idesc128 = FP4 ? instr_desc_mxf4<LY::TILE_M, BN / 2>()
+                                              : instr_desc<LY::TILE_M, BN / 2>(1u);
             // operand stage e's descriptor: the start-address field (bytes >> 4)
             // moves by EB_BYTES >> 4 per stage; every stage lies below 256 KB,
             // so no carry
@@ -844,10 +877,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             bool ok = true;
             // a tile's k stages are loaded one tile ahead (batched: from the
             // work list in global memory, off the issue path)
-            int nks_next = my_tiles > 0 ? tile_nks<BATCHED, PAIR>(p, 0) : 0;
+            TileK tk_next = my_tiles > 0 ? tile_k<BATCHED, PAIR>(p, 0) : TileK{0, 0};
             for (int i = 0; ok && i < my_tiles; i++) {
-                const int nks = nks_next;
-                if (i + 1 < my_tiles) nks_next = tile_nks<BATCHED, PAIR>(p, i + 1);
+                const int nks = tk_next.nks;
+                const uint32_t id = BATCHED && tk_next.n128 ? idesc128 : idesc;
+                if (i + 1 < my_tiles) tk_next = tile_k<BATCHED, PAIR>(p, i + 1);
                 int kin = 0;
                 for (int ks = 0; ks < nks; ks += SUB, pit++) {
                     // Every producer fills the slots in order, so one wait on
@@ -876,6 +910,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (group || kin == 0) tc_fence_after();
 #pragma unroll
                     for (int sub = 0; sub < SUB; sub++) {
+                        // batched: an odd k-stage count ends in half a packed
+                        // stage, whose second operand stage is all padding
+                        if (BATCHED && sub > 0 && ks + sub >= nks) break;
                         const int e = 2 * q + sub;
                         const uint32_t ta = tmem + (uint32_t)(A_COL + e * A_STAGE_COLS);
                         const uint64_t db = db_base + (uint64_t)(e * (LY::EB_BYTES >> 4));
@@ -884,11 +921,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                             const uint32_t acc = (kin > 0 || sub > 0 || j > 0) ? 1u : 0u;
                             if (FP4)
                                 mma_f4_ta<PAIR>(tmem + ACC_COL, ta + j * A_MMA_COLS, db + 2 * j,
-                                                idesc, tmem + SF_COL, tmem + SF_COL + SF_COLS / 2,
-                                                acc);
+                                                BATCHED ? id : idesc, tmem + SF_COL,
+                                                tmem + SF_COL + SF_COLS / 2, acc);
                             else
                                 mma_f8_ta<PAIR>(tmem + ACC_COL, ta + j * A_MMA_COLS, db + 2 * j,
-                                                idesc, acc);
+                                                BATCHED ? id : idesc, acc);
                         }
                     }
                     mma_commit<PAIR>(empty_o(q));
@@ -922,6 +959,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             const Tile tc = tile_get<BATCHED, PAIR>(p, i, &tmA, &tmB);
             const int nseg = (tc.nks + kchunk - 1) / kchunk;
             const bool gf2 = tc.op == OP_GF2;
+            // an N = 128 tile writes no accumulator column past 128: the warps
+            // that drain those columns only hand the accumulator back
+            const bool idle = BATCHED && PAIR && tc.n128 && chalf == 1;
             uint32_t words[CW];
 #pragma unroll
             for (int c = 0; c < CW; c++) words[c] = 0u;
@@ -931,6 +971,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                     break;
                 }
                 tc_fence_after();
+                if (idle) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) arrive_leader(acc_empty);
+                    continue;
+                }
                 // 64 columns per load: half the load-wait round trips of 32
 #pragma unroll
                 for (int c = 0; c < CW; c += 2) {

@@ -191,3 +191,36 @@ def ctypes_ref(x):
     import ctypes
 
     return ctypes.byref(x)
+
+
+def test_batched_plan_arguments_need_no_gpu(built_lib):
+    """Per-problem path requests and the plan queries are checked before any
+    CUDA call: unknown paths, two different tensor paths in one plan, the
+    integer tensor path sm_103a lacks, null plans and out-of-range problems."""
+    import ctypes
+
+    import paper_1909_01554_gb300 as bmm
+
+    L = bmm.lib()
+    a = 1 << 20  # never dereferenced: every case fails its argument checks first
+    P = ctypes.c_void_p * 2
+    I64 = ctypes.c_int64 * 2
+    I32 = ctypes.c_int32 * 2
+    ops, A, B, C = I32(0, 1), P(a, a), P(a, a), P(a + 4096, a + 8192)
+    sz = I64(64, 64)
+    h = ctypes.c_void_p(0)
+    for paths, want in (((9, bmm.PATH_AUTO), bmm.ERR_INVALID),
+                        ((bmm.PATH_TC_FP4_PAIR, bmm.PATH_TC_FP8_PAIR), bmm.ERR_INVALID),
+                        ((bmm.PATH_TC_I8, bmm.PATH_POPC), bmm.ERR_UNSUPPORTED)):
+        assert L.bmm_batched_plan_create_paths(2, ops, A, B, C, sz, sz, sz, I32(*paths),
+                                               ctypes.byref(h)) == want
+        assert not h.value
+    assert L.bmm_batched_plan_create_paths(2, ops, A, B, C, sz, sz, sz, None,
+                                           ctypes.byref(h)) == bmm.ERR_INVALID
+    assert L.bmm_batched_plan_create_paths(2, ops, A, B, C, I64(64, 100), sz, sz,
+                                           I32(0, 0), ctypes.byref(h)) == bmm.ERR_INVALID
+    assert L.bmm_batched_plan_choice(None, 0, ctypes.byref(bmm.BatchedChoice())) == bmm.ERR_INVALID
+    assert L.bmm_batched_plan_stats(None, ctypes.byref(bmm.BatchedStats())) == bmm.ERR_INVALID
+    assert L.bmm_batched_model(9, ctypes.byref(bmm.BatchedModel())) == bmm.ERR_INVALID
+    assert L.bmm_batched_model(bmm.PATH_TC_I8, ctypes.byref(bmm.BatchedModel())) == \
+        bmm.ERR_UNSUPPORTED

@@ -82,8 +82,93 @@ def test_batched_plan_auto_path_is_fastest_tensor_path():
     plan = bmm.BatchedPlan([s[3] for s in SMALL[:2]], [d[0] for d in dev], [d[1] for d in dev],
                            [d[2] for d in dev], [s[0] for s in SMALL[:2]],
                            [s[1] for s in SMALL[:2]], [s[2] for s in SMALL[:2]])
-    assert plan.path() == bmm.plan(bmm.GF2, 4096, 4096, 4096, depth=0)["path"]
-    assert plan.path() == bmm.PATH_TC_FP4_PAIR
+    st = plan.stats()
+    assert st["tensor_path"] == bmm.plan(bmm.GF2, 4096, 4096, 4096, depth=0)["path"]
+    assert st["tensor_path"] == bmm.PATH_TC_FP4_PAIR
+    plan.destroy()
+
+
+def run_plan(shapes, seed, **kw):
+    host, dev = make_batch(shapes, seed)
+    plan = bmm.BatchedPlan([s[3] for s in shapes], [d[0] for d in dev], [d[1] for d in dev],
+                           [d[2] for d in dev], [s[0] for s in shapes], [s[1] for s in shapes],
+                           [s[2] for s in shapes], **kw)
+    plan.run()
+    bmm.stream_status()
+    return host, dev, plan
+
+
+def test_batched_model_is_measured():
+    """The cost model the plans decide with is measured on this device, per
+    stage of k and per tile of each kernel."""
+    m = bmm.batched_model(bmm.PATH_POPC)
+    assert m["measured"] == 1 and m["popc_units"] > 0
+    assert m["popc_stage_ns"] > 0 and m["popc_tile_ns"] >= 0
+    if bmm.device_supported():
+        for path in bmm.TENSOR_PATHS:
+            t = bmm.batched_model(path)
+            assert t["measured"] == 1 and t["path"] == path and t["tensor_units"] > 0
+            assert t["tensor_stage_ns"] > 0 and t["tensor_stage_n128_ns"] > 0
+            assert t["tensor_tile_ns"] >= 0
+
+
+def test_batched_per_problem_paths():
+    """Base cases named per problem (CUDA cores, the tensor path, or left to
+    the model) in one plan: each problem runs where it was sent, all exact."""
+    if not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    req = [bmm.PATH_POPC, bmm.PATH_TC_FP4_PAIR, bmm.PATH_AUTO, bmm.PATH_POPC,
+           bmm.PATH_TC_FP4_PAIR, bmm.PATH_AUTO, bmm.PATH_POPC, bmm.PATH_TC_FP4_PAIR]
+    host, dev, plan = run_plan(SMALL, 53, paths=req)
+    st = plan.stats()
+    for i, r in enumerate(req):
+        c = plan.choice(i)
+        if r != bmm.PATH_AUTO:
+            assert c["path"] == r, (i, c)
+        assert c["path"] in (bmm.PATH_POPC, bmm.PATH_TC_FP4_PAIR)
+        assert c["strassen_depth"] == 0
+    assert st["popc_problems"] >= 3 and st["tensor_problems"] >= 3
+    assert st["popc_problems"] + st["tensor_problems"] == len(SMALL)
+    check_all(SMALL, host, dev)
+    plan.destroy()
+    with pytest.raises(bmm.BmmError) as e:  # two tensor paths in one plan
+        bmm.BatchedPlan([s[3] for s in SMALL[:2]], [d[0] for d in dev[:2]],
+                        [d[1] for d in dev[:2]], [d[2] for d in dev[:2]],
+                        [s[0] for s in SMALL[:2]], [s[1] for s in SMALL[:2]],
+                        [s[2] for s in SMALL[:2]],
+                        paths=[bmm.PATH_TC_FP4_PAIR, bmm.PATH_TC_FP8_PAIR])
+    assert e.value.status == bmm.ERR_INVALID
+
+
+# Tail tiles and half k stages: n = 256 j + 64 or + 128 leaves at most 128
+# columns in the last column tile (N = 128 where the model measured that form
+# cheaper); k = 768 and 1280 are 3 and 5 stages of 256 bits (the last packed
+# stage of 512 is half padding, not multiplied), k = 320 and 448 pad to 384
+# and 512; m = 320 and 704 leave part of the last 256-row tile empty.
+TAILS = [(320, 768, 320, 0), (704, 1280, 384, 1), (256, 256, 128, 0), (448, 320, 64, 1),
+         (320, 448, 576, 0), (1024, 1792, 1152, 1), (64, 768, 192, 0), (512, 256, 640, 1)]
+
+
+@pytest.mark.parametrize("path", list(bmm.TENSOR_PATHS))
+def test_batched_tail_tiles_and_half_stages(path):
+    if not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    model = bmm.batched_model(path)
+    host, dev, plan = run_plan(TAILS, 59, path=path)
+    kstep = 256 if path == bmm.PATH_TC_FP4_PAIR else 128
+    narrow = model["tensor_stage_n128_ns"] < model["tensor_stage_ns"]
+    for i, (m, k, n, op) in enumerate(TAILS):
+        c = plan.choice(i)
+        assert c["path"] == path and c["k_step"] == kstep
+        kpad = (k // 64 + 1) // 2 * 2 * 64
+        assert c["k_steps"] == -(-kpad // kstep)
+        tail = n - (-(-n // 256) - 1) * 256
+        assert c["tail_n"] == (128 if narrow and tail <= 128 else 256), (i, c)
+    st = plan.stats()
+    if narrow:
+        assert st["tensor_tiles_n128"] > 0
+    assert st["macs_issued"] >= st["macs_needed"]
+    check_all(TAILS, host, dev)
     plan.destroy()
 
 
@@ -149,10 +234,16 @@ def test_batched_config5_shapes_sampled():
         dev.append((A, B, C))
         rows.append(sorted(rng.choice(m, 2, replace=False).tolist()))
     torch.cuda.synchronize()
-    bmm.batched([s[3] for s in shapes], [d[0] for d in dev], [d[1] for d in dev],
-                [d[2] for d in dev], [s[0] for s in shapes], [s[1] for s in shapes],
-                [s[2] for s in shapes])
+    plan = bmm.BatchedPlan([s[3] for s in shapes], [d[0] for d in dev], [d[1] for d in dev],
+                           [d[2] for d in dev], [s[0] for s in shapes], [s[1] for s in shapes],
+                           [s[2] for s in shapes])
+    st = plan.stats()
+    assert st["problems"] == 2048
+    assert st["macs_needed"] == float(sum(m * k * n for m, k, n, _ in shapes))
+    assert st["macs_issued"] >= st["macs_needed"]
+    plan.run()
     bmm.stream_status()
+    plan.destroy()
     full = set(rng.choice(2048, 12, replace=False).tolist())
     for i, (m, k, n, op) in enumerate(shapes):
         seed = (5 << 16) + i

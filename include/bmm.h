@@ -86,11 +86,14 @@ typedef struct {
                                 kernel (a level shifted into the inner layer, Sec. 3.15),
                                 which forms each of the 7 products' operands from
                                 the quadrants as it stages them and folds the products
-                                into the C quadrants in registers (no leaf operands or
+                                into the C quadrants on chip (no leaf operands or
                                 leaf products in HBM). Binary product on the CUDA-core
-                                path only (BMM_PATH_POPC, or AUTO where it resolves
-                                there), else BMM_ERR_UNSUPPORTED; a plan without Strassen
-                                levels ignores it. 0 (default): every level in XOR passes */
+                                path (BMM_PATH_POPC) or the e2m1 tensor path
+                                (BMM_PATH_TC_FP4_PAIR; k is then padded so that every
+                                quadrant's k is a multiple of 512 bits), or AUTO where
+                                it resolves to one of them; other paths give
+                                BMM_ERR_UNSUPPORTED; a plan without Strassen levels
+                                ignores it. 0 (default): every level in XOR passes */
 } bmm_opts;
 
 /* Fills opts with the defaults (auto path, auto depth, self-inverse variant). */

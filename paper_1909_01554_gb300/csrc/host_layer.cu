@@ -67,9 +67,11 @@ uint64_t product_scratch(int op, int64_t m, int64_t k, int64_t n, const bmm_opts
     // the path the device plan resolves AUTO to (the CUDA cores where the
     // device has no tensor-core path, and without a device)
     const int path = o.path == BMM_PATH_AUTO ? auto_path() : o.path;
-    const int od = (o.kernel_level == 1 && d > 0 && path == BMM_PATH_POPC) ? d - 1 : d;
+    const bool kl = o.kernel_level == 1 && d > 0 &&
+                    (path == BMM_PATH_POPC || path == BMM_PATH_TC_FP4_PAIR);
+    const int od = kl ? d - 1 : d;
     const int serial = od > 2 ? od - 2 : 0;
-    const int64_t unit = (int64_t)128 << d;
+    const int64_t unit = (int64_t)(kl ? 512 : 128) << d;
     const int64_t kp = path == BMM_PATH_POPC ? k : (k + unit - 1) / unit * unit;
     return workspace_padded(m, k, kp, n, od, serial);
 }

@@ -120,5 +120,12 @@ cudaError_t launch_popc_level(const uint64_t* A, int64_t lda, int64_t strideA, c
                               int64_t ldb, int64_t strideB, uint64_t* C, int64_t ldc,
                               int64_t strideC, int64_t count, int64_t m, int64_t k, int64_t n,
                               const LevelMasks& masks, cudaStream_t s);
+// The same on the tensor cores (e2m1 operands, SM pairs): every quadrant's k a
+// whole number of 512-bit packed stages (k a multiple of 1024), even pitches
+// and strides; BMM_ERR_UNSUPPORTED otherwise or without the tensor path.
+bmm_status run_tc_level(const uint64_t* A, int64_t lda, int64_t strideA, const uint64_t* Bt,
+                        int64_t ldb, int64_t strideB, uint64_t* C, int64_t ldc, int64_t strideC,
+                        int64_t count, int64_t m, int64_t k, int64_t n, const LevelMasks& masks,
+                        cudaStream_t s);
 
 }  // namespace bmm

@@ -125,6 +125,8 @@ struct Exec {
             std::memcpy(lm.xi, xi, sizeof xi);
             std::memcpy(lm.eta, eta, sizeof eta);
             std::memcpy(lm.zeta, zeta, sizeof zeta);
+            if (p.path == BMM_PATH_TC_FP4_PAIR)
+                return run_tc_level(A, lda, sa, B, ldb, sb, C, ldc, sc, count, m, k, n, lm, s);
             BMM_CUDA_TRY(launch_popc_level(A, lda, sa, B, ldb, sb, C, ldc, sc, count, m, k, n, lm,
                                            s));
             return BMM_OK;
@@ -242,15 +244,19 @@ bmm_status make_plan(int op, int64_t m, int64_t k, int64_t n, const bmm_opts* op
     // base-case path (auto_path below); the tensor paths pad k so that every
     // leaf's k is a multiple of 128 bits
     p.path = o.path == BMM_PATH_AUTO ? auto_path() : o.path;
+    // The innermost level inside the base-case kernel: the CUDA-core kernel
+    // and the e2m1 SM-pair kernel have that form; a plan without Strassen
+    // levels has no level to move.
+    p.kernel_level = (o.kernel_level && p.depth > 0) ? 1 : 0;
+    if (p.kernel_level && p.path != BMM_PATH_POPC && p.path != BMM_PATH_TC_FP4_PAIR)
+        return BMM_ERR_UNSUPPORTED;
     p.kp = k;
     if (is_tc_path(p.path)) {
-        const int64_t unit = (int64_t)128 << p.depth;  // leaf k a multiple of 128 bits
+        // leaf k a multiple of 128 bits; with the level in the tensor kernel,
+        // of its 512-bit packed stage (a quadrant's copies stay inside it)
+        const int64_t unit = (int64_t)(p.kernel_level ? 512 : 128) << p.depth;
         p.kp = (k + unit - 1) / unit * unit;
     }
-    // The innermost level inside the base-case kernel: the CUDA-core kernel
-    // has that form; a plan without Strassen levels has no level to move.
-    p.kernel_level = (o.kernel_level && p.depth > 0) ? 1 : 0;
-    if (p.kernel_level && p.path != BMM_PATH_POPC) return BMM_ERR_UNSUPPORTED;
     const int od = p.depth - p.kernel_level;  // levels run by the XOR passes
     // depth-first levels: at least od - MAX_MERGED; more while the
     // breadth-first scratch does not fit in free device memory.

@@ -107,7 +107,11 @@ constexpr int TMEM_COLS = 512;
 // each CTA expands only its half of the Bt rows, and the pair's MMAs read
 // both halves: per SM, half the shared-memory traffic and a third less
 // expansion work for the same number of MACs.
-template <bool PAIR, bool FP4>
+// LEVEL: the in-kernel Strassen level (below). Its packed stages hold up to
+// six quadrant tiles (the A quadrants one product combines, then its Bt
+// quadrants; at most six for every variant's products), so the ring is two
+// packed stages deep.
+template <bool PAIR, bool FP4, bool LEVEL = false>
 struct Lay {
     static constexpr int KS = FP4 ? 256 : 128;  // k (bits) per operand stage
     static constexpr int KP = SUB * KS;         // k (bits) per packed (TMA) stage
@@ -115,7 +119,7 @@ struct Lay {
     // ring depths: packed stages (shared) and operand stages (Bt in shared,
     // A in TMEM); a pair's smaller operand stages leave room for deeper rings.
     // The e2m1 form gives up two operand stages of TMEM to the block scales.
-    static constexpr int PSTAGES = PAIR ? 6 : 4;
+    static constexpr int PSTAGES = LEVEL ? 2 : PAIR ? 6 : 4;
     static constexpr int ESTAGES = PAIR ? (FP4 ? 6 : 8) : 4;
     // operand slots: the two operand stages one packed stage fills
     static constexpr int OSLOTS = ESTAGES / SUB;
@@ -138,10 +142,18 @@ struct Lay {
     static constexpr int PA_BYTES = BM * KP / 8;       // packed A per packed stage
     static constexpr int PB_BYTES = BROWS * KP / 8;    // packed Bt per packed stage
     static constexpr int EB_BYTES = BROWS * 128;       // expanded Bt per operand stage
+    static constexpr int QTILES = 6;                   // LEVEL: quadrant tiles per stage
     static constexpr int OFF_EB = 0;
     static constexpr int OFF_PA = OFF_EB + ESTAGES * EB_BYTES;
-    static constexpr int OFF_PB = OFF_PA + PSTAGES * PA_BYTES;
-    static constexpr int OFF_BAR = OFF_PB + PSTAGES * PB_BYTES;
+    static constexpr int OFF_PB = OFF_PA + PSTAGES * PA_BYTES;  // (not LEVEL)
+    static constexpr int PSTAGE_BYTES = QTILES * PA_BYTES;      // LEVEL: one packed stage
+    // LEVEL: every epilogue thread's words of the four C quadrants (4 x 4
+    // words, lane-interleaved), in shared memory beside the registers the
+    // accumulator loads need
+    static constexpr int QOUT_BYTES = LEVEL ? EPI_WARPS * 32 * 16 * 4 : 0;
+    static constexpr int OFF_QOUT = LEVEL ? OFF_PA + PSTAGES * PSTAGE_BYTES : 0;
+    static constexpr int OFF_BAR =
+        LEVEL ? OFF_QOUT + QOUT_BYTES : OFF_PB + PSTAGES * PB_BYTES;
     static constexpr int OFF_TMEM_SLOT = OFF_BAR + NBARS * 8;
     static constexpr int SMEM_BYTES = OFF_TMEM_SLOT + 16 + 1024;  // + alignment slack
     static_assert(EB_BYTES % 1024 == 0, "swizzle atoms stay 1024-byte aligned");
@@ -151,6 +163,7 @@ struct Lay {
                   "an MMA reads 32 bytes of k per row");
     static_assert(ESTAGES % SUB == 0, "a packed stage's operand stages are adjacent in TMEM");
     static_assert(SMEM_BYTES <= 227 * 1024, "shared memory budget");
+    static_assert(!LEVEL || (PAIR && PA_BYTES == PB_BYTES), "LEVEL: equal quadrant tiles");
 };
 
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s
@@ -527,6 +540,13 @@ struct Params {
     int kchunk;  // stages per flush (both forms)
     uint32_t* err;
     Spread sp;
+    // LEVEL: each leaf is a block of 2m x 2k times 2k x 2n bits whose seven
+    // quadrant products run here (m, n, nks: one quadrant product); qkw:
+    // words of k per quadrant; nibble h of xi4 / eta4: the A / B quadrants
+    // product h combines; bits 7q..7q+6 of zeta7: the products C quadrant q
+    // sums.
+    uint32_t xi4, eta4, zeta7;
+    int qkw;
 };
 
 // Everything a role needs about one output tile.
@@ -613,11 +633,25 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* m) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
 }
 
-template <bool BATCHED, bool PAIR, bool FP4>
+// The in-kernel Strassen level (LEVEL; a level shifted from the expanding
+// and compressing passes into the inner layer, Sec. 3.15), binary product
+// only: every leaf of the launch is a block of 2m x 2k times 2k x 2n bits,
+// and a CTA pair takes one 256 x 256 tile position of the quadrant-sized
+// product and runs the block's seven quadrant products there, one after the
+// other. For product h the TMA producer loads, per packed stage, the tiles
+// of the A quadrants that xi_h = alpha_h phi selects and of the Bt quadrants
+// that eta_h = beta_h psi selects (the combined operators of Eqs. mb-* /
+// ab-* / sw-*), the expansion warps XOR them as they expand, so the seven
+// operands never exist in HBM, and the epilogue XORs the product's parity
+// bits into the C quadrants that zeta = chi gamma sends it to, in
+// registers; the four quadrant words of the position leave once, after the
+// seventh product.
+template <bool BATCHED, bool PAIR, bool FP4, bool LEVEL = false>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_nt_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const Params p) {
-    using LY = Lay<PAIR, FP4>;
+    static_assert(!LEVEL || (!BATCHED && PAIR), "the in-kernel level runs on SM pairs");
+    using LY = Lay<PAIR, FP4, LEVEL>;
     constexpr int PSTAGES = LY::PSTAGES, OSLOTS = LY::OSLOTS, KP = LY::KP;
     constexpr int BEXP_WARPS = LY::BEXP_WARPS, EPI_WARP0 = LY::EPI_WARP0,
                   EPI_WARPS = LY::EPI_WARPS;
@@ -679,7 +713,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (BATCHED)
         total_pit = p.cta_ptr[unit_count<PAIR>() + 1 + unit_id<PAIR>()];
     else
-        total_pit = my_tiles * (p.nks / SUB);
+        total_pit = my_tiles * (LEVEL ? 7 : 1) * (p.nks / SUB);
+    // LEVEL: a packed stage's quadrant tiles, A's first (sub-buffer j)
+    auto qtile = [&](int s, int j) {
+        return (uint32_t)(LY::OFF_PA + s * LY::PSTAGE_BYTES + j * LY::PA_BYTES);
+    };
 
     if (warp == TMA_WARP) {
         // ---------------------------------------------------- TMA producer
@@ -707,6 +745,35 @@ __global__ void __launch_bounds__(THREADS, 1)
                 // an N = 128 tile takes 64 of its columns from each CTA of a pair
                 const int brow =
                     tc.tn * BN + (int)rank * (BATCHED && tc.n128 ? LY::BROWS / 2 : LY::BROWS);
+                if (LEVEL) {
+                    // A quadrant (r, c) at rows r m, words c qkw; B block (r, c)
+                    // is stored transposed, as Bt rows c n, words r qkw
+                    for (int h = 0; ok && h < 7; h++) {
+                        const uint32_t xa = (p.xi4 >> (4 * h)) & 0xFu;
+                        const uint32_t xb = (p.eta4 >> (4 * h)) & 0xFu;
+                        const uint32_t bytes = (uint32_t)(__popc(xa) + __popc(xb)) * LY::PA_BYTES;
+                        for (int kp = 0; kp < tc.nks / SUB; kp++, pit++) {
+                            const int s = pit % PSTAGES;
+                            if (!mbar_wait(empty_p(s), ((pit / PSTAGES) & 1) ^ 1, p.err)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_arrive_tx(full_p(s), bytes);
+                            int j = 0;
+                            for (int q = 0; q < 4; q++)
+                                if ((xa >> q) & 1u)
+                                    tma_load_3d(sbase + qtile(s, j++), tc.ma,
+                                                (q & 1) * p.qkw + kp * (KP / 64),
+                                                (q >> 1) * tc.m + arow, tc.leaf, full_p(s));
+                            for (int q = 0; q < 4; q++)
+                                if ((xb >> q) & 1u)
+                                    tma_load_3d(sbase + qtile(s, j++), tc.mb,
+                                                (q >> 1) * p.qkw + kp * (KP / 64),
+                                                (q & 1) * tc.n + brow, tc.leaf, full_p(s));
+                        }
+                    }
+                    continue;
+                }
                 for (int kp = 0; kp < (tc.nks + SUB - 1) / SUB; kp++, pit++) {
                     const int s = pit % PSTAGES;
                     if (!mbar_wait(empty_p(s), ((pit / PSTAGES) & 1) ^ 1, p.err)) {
@@ -734,6 +801,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         // A quarter-warp holds the 8 chunks of one row: 8 distinct bank groups.
         const int h = lane >> 4, rr = (lane >> 3) & 1, wl = lane & 7;
         const Spread sp = p.sp;
+        int lv_k = 0, lv_h = 0;  // LEVEL: packed stage within the product, the product
         for (int pit = 0; pit < total_pit; pit++) {
             const int s = pit % PSTAGES;
             const int q = pit % OSLOTS;
@@ -741,13 +809,31 @@ __global__ void __launch_bounds__(THREADS, 1)
                 !mbar_wait(empty_o(q), ((pit / OSLOTS) & 1) ^ 1, p.err))
                 break;
             constexpr int ITEMS = (LY::BROWS / 2) / BEXP_WARPS;
-            const uint32_t* pb =
-                reinterpret_cast<const uint32_t*>(smem + LY::OFF_PB + s * LY::PB_BYTES);
             uint8_t* eb = smem + LY::OFF_EB + (2 * q + h) * LY::EB_BYTES;
             uint32_t x[ITEMS];
+            if (LEVEL) {
+                // S_h: the XOR of the Bt quadrant tiles, stored after A's
+                const int j0 = __popc((p.xi4 >> (4 * lv_h)) & 0xFu);
+                const int nb = __popc((p.eta4 >> (4 * lv_h)) & 0xFu);
 #pragma unroll
-            for (int i = 0; i < ITEMS; i++)
-                x[i] = pb[((warp + BEXP_WARPS * i) * 2 + rr) * 16 + 8 * h + wl];
+                for (int i = 0; i < ITEMS; i++) x[i] = 0u;
+                for (int j = 0; j < nb; j++) {
+                    const uint32_t* pb = reinterpret_cast<const uint32_t*>(smem + qtile(s, j0 + j));
+#pragma unroll
+                    for (int i = 0; i < ITEMS; i++)
+                        x[i] ^= pb[((warp + BEXP_WARPS * i) * 2 + rr) * 16 + 8 * h + wl];
+                }
+                if (++lv_k == p.nks / SUB) {
+                    lv_k = 0;
+                    if (++lv_h == 7) lv_h = 0;
+                }
+            } else {
+                const uint32_t* pb =
+                    reinterpret_cast<const uint32_t*>(smem + LY::OFF_PB + s * LY::PB_BYTES);
+#pragma unroll
+                for (int i = 0; i < ITEMS; i++)
+                    x[i] = pb[((warp + BEXP_WARPS * i) * 2 + rr) * 16 + 8 * h + wl];
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(empty_p(s));
 #pragma unroll
@@ -821,16 +907,40 @@ __global__ void __launch_bounds__(THREADS, 1)
             tmem_st64(tmem + tlane + (uint32_t)SF_COL, f);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         }
+        int lv_k = 0, lv_h = 0;  // LEVEL: packed stage within the product, the product
         for (int pit = 0; pit < total_pit; pit++) {
             const int s = pit % PSTAGES;
             const int q = pit % OSLOTS;
             if (!mbar_wait(full_p(s), (pit / PSTAGES) & 1, p.err)) break;
-            const uint4* src = reinterpret_cast<const uint4*>(smem + LY::OFF_PA +
-                                                              s * LY::PA_BYTES + row * (KP / 8));
             constexpr int NV = KP / 128;  // 16-byte vectors per packed row
             uint4 xv[NV];
+            if (LEVEL) {
+                // T_h: the XOR of the A quadrant tiles
+                const int na = __popc((p.xi4 >> (4 * lv_h)) & 0xFu);
 #pragma unroll
-            for (int v = 0; v < NV; v++) xv[v] = src[v];
+                for (int v = 0; v < NV; v++) xv[v] = make_uint4(0u, 0u, 0u, 0u);
+                for (int j = 0; j < na; j++) {
+                    const uint4* src =
+                        reinterpret_cast<const uint4*>(smem + qtile(s, j) + row * (KP / 8));
+#pragma unroll
+                    for (int v = 0; v < NV; v++) {
+                        const uint4 t = src[v];
+                        xv[v].x ^= t.x;
+                        xv[v].y ^= t.y;
+                        xv[v].z ^= t.z;
+                        xv[v].w ^= t.w;
+                    }
+                }
+                if (++lv_k == p.nks / SUB) {
+                    lv_k = 0;
+                    if (++lv_h == 7) lv_h = 0;
+                }
+            } else {
+                const uint4* src = reinterpret_cast<const uint4*>(smem + LY::OFF_PA +
+                                                                  s * LY::PA_BYTES + row * (KP / 8));
+#pragma unroll
+                for (int v = 0; v < NV; v++) xv[v] = src[v];
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(empty_p(s));
             if (!mbar_wait(empty_o(q), ((pit / OSLOTS) & 1) ^ 1, p.err)) break;
@@ -878,10 +988,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             // a tile's k stages are loaded one tile ahead (batched: from the
             // work list in global memory, off the issue path)
             TileK tk_next = my_tiles > 0 ? tile_k<BATCHED, PAIR>(p, 0) : TileK{0, 0};
-            for (int i = 0; ok && i < my_tiles; i++) {
+            // LEVEL: every tile position runs seven products, each an
+            // accumulator tile of its own
+            const int mma_tiles = LEVEL ? 7 * my_tiles : my_tiles;
+            for (int i = 0; ok && i < mma_tiles; i++) {
                 const int nks = tk_next.nks;
                 const uint32_t id = BATCHED && tk_next.n128 ? idesc128 : idesc;
-                if (i + 1 < my_tiles) tk_next = tile_k<BATCHED, PAIR>(p, i + 1);
+                if (i + 1 < mma_tiles) tk_next = tile_k<BATCHED, PAIR>(p, i + 1);
                 int kin = 0;
                 for (int ks = 0; ks < nks; ks += SUB, pit++) {
                     // Every producer fills the slots in order, so one wait on
@@ -962,9 +1075,25 @@ __global__ void __launch_bounds__(THREADS, 1)
             // an N = 128 tile writes no accumulator column past 128: the warps
             // that drain those columns only hand the accumulator back
             const bool idle = BATCHED && PAIR && tc.n128 && chalf == 1;
-            uint32_t words[CW];
+            // LEVEL: this thread's words of the four C quadrants, summed over
+            // the position's seven products: word (q, c) at qo[(CW q + c) 32]
+            static_assert(!LEVEL || CW == 4, "four words per quadrant");
+            uint32_t* qo = reinterpret_cast<uint32_t*>(smem + LY::OFF_QOUT) +
+                           (warp - EPI_WARP0) * 32 * 16 + lane;
+            if (LEVEL)
 #pragma unroll
-            for (int c = 0; c < CW; c++) words[c] = 0u;
+                for (int j = 0; j < 16; j++) qo[32 * j] = 0u;
+            uint32_t out[1][CW];
+#pragma unroll
+            for (int c = 0; c < CW; c++) out[0][c] = 0u;
+            for (int h = 0; ok && h < (LEVEL ? 7 : 1); h++) {
+            // LEVEL: the C quadrants product h goes to (bit q)
+            uint32_t zq = 0;
+            if (LEVEL)
+                for (int q = 0; q < 4; q++) zq |= ((p.zeta7 >> (7 * q + h)) & 1u) << q;
+            uint32_t words[LEVEL ? 1 : CW];
+#pragma unroll
+            for (int c = 0; c < (LEVEL ? 1 : CW); c++) words[c] = 0u;
             for (int g = 0; g < nseg; g++, seg++) {
                 if (!mbar_wait(acc_full, seg & 1, p.err)) {
                     ok = false;
@@ -975,6 +1104,28 @@ __global__ void __launch_bounds__(THREADS, 1)
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) arrive_leader(acc_empty);
+                    continue;
+                }
+                if (LEVEL) {
+                    // parities are XOR-linear: each chunk folds straight into
+                    // the quadrants product h goes to
+#pragma unroll
+                    for (int c = 0; c < CW; c += 2) {
+                        uint32_t v[64];
+                        tmem_ld64(tmem + tlane + (uint32_t)(ACC_COL + 32 * (CW * chalf + c)), v);
+                        if (c + 2 == CW) {
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) arrive_leader(acc_empty);
+                        }
+                        const uint32_t b0 = pack_bits<OP_GF2>(v), b1 = pack_bits<OP_GF2>(v + 32);
+#pragma unroll
+                        for (int q = 0; q < 4; q++)
+                            if ((zq >> q) & 1u) {
+                                qo[32 * (CW * q + c)] ^= b0;
+                                qo[32 * (CW * q + c + 1)] ^= b1;
+                            }
+                    }
                     continue;
                 }
                 // 64 columns per load: half the load-wait round trips of 32
@@ -998,17 +1149,38 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                 }
             }
+            if (!LEVEL) {
+#pragma unroll
+                for (int c = 0; c < CW; c++) out[0][c] = words[c];
+            }
+            }
             if (!ok) break;
             const int64_t row =
                 (int64_t)tc.tm * LY::TILE_M + (int64_t)rank * BM + 32 * quarter + lane;
-            if (row < tc.m) {
+            if (LEVEL) {
+                // quadrant (r, c) of the block's C: rows r m, words c n/64
+                const int64_t w0 = (int64_t)tc.tn * (BN / 64) + chalf * (CW / 2);
+                const int64_t nw = tc.n / 64;
+                if (row < tc.m) {
+#pragma unroll
+                    for (int q = 0; q < (LEVEL ? 4 : 1); q++) {
+                        uint64_t* crow = tc.C + ((q >> 1) * (int64_t)tc.m + row) * tc.ldc +
+                                         (q & 1) * nw;
+#pragma unroll
+                        for (int c = 0; c < CW / 2; c++)
+                            if (w0 + c < nw)
+                                crow[w0 + c] = (uint64_t)qo[32 * (CW * q + 2 * c)] |
+                                               ((uint64_t)qo[32 * (CW * q + 2 * c + 1)] << 32);
+                    }
+                }
+            } else if (row < tc.m) {
                 uint64_t* crow = tc.C + row * tc.ldc;
                 const int64_t w0 = (int64_t)tc.tn * (BN / 64) + chalf * (CW / 2);
                 const int64_t nw = tc.n / 64;
 #pragma unroll
                 for (int c = 0; c < CW / 2; c++)
                     if (w0 + c < nw)
-                        crow[w0 + c] = (uint64_t)words[2 * c] | ((uint64_t)words[2 * c + 1] << 32);
+                        crow[w0 + c] = (uint64_t)out[0][2 * c] | ((uint64_t)out[0][2 * c + 1] << 32);
             }
         }
     }
@@ -1068,7 +1240,7 @@ int current_device() {
 // Per-device one-time setup (function attributes and occupancy are per device).
 std::mutex g_setup_mu;
 
-template <bool BATCHED, bool PAIR, bool FP4>
+template <bool BATCHED, bool PAIR, bool FP4, bool LEVEL = false>
 cudaError_t set_smem_attr() {
     static bool done[MAX_DEVICES] = {false};
     static cudaError_t err[MAX_DEVICES];
@@ -1076,9 +1248,9 @@ cudaError_t set_smem_attr() {
     if (d < 0 || d >= MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_setup_mu);
     if (!done[d]) {
-        err[d] = cudaFuncSetAttribute(tc_nt_kernel<BATCHED, PAIR, FP4>,
+        err[d] = cudaFuncSetAttribute(tc_nt_kernel<BATCHED, PAIR, FP4, LEVEL>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      Lay<PAIR, FP4>::SMEM_BYTES);
+                                      Lay<PAIR, FP4, LEVEL>::SMEM_BYTES);
         done[d] = true;
     }
     return err[d];
@@ -1126,11 +1298,11 @@ int pair_slots() {
 }
 
 // units: CTAs (single) or CTA pairs (PAIR) to launch.
-template <bool BATCHED, bool PAIR, bool FP4>
+template <bool BATCHED, bool PAIR, bool FP4, bool LEVEL = false>
 cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const Params& prm, int units,
                       cudaStream_t s) {
     static_assert(PAIR || !FP4, "the e2m1 form runs on SM pairs");
-    const cudaError_t e = set_smem_attr<BATCHED, PAIR, FP4>();
+    const cudaError_t e = set_smem_attr<BATCHED, PAIR, FP4, LEVEL>();
     if (e != cudaSuccess) return e;
     if (!PAIR) {
         tc_nt_kernel<BATCHED, false, false>
@@ -1138,9 +1310,33 @@ cudaError_t launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, const Params
         return cudaGetLastError();
     }
     cudaLaunchAttribute at[1];
-    cudaLaunchConfig_t cfg = pair_config((unsigned)units, Lay<PAIR, FP4>::SMEM_BYTES, at);
+    cudaLaunchConfig_t cfg = pair_config((unsigned)units, Lay<PAIR, FP4, LEVEL>::SMEM_BYTES, at);
     cfg.stream = s;
-    return cudaLaunchKernelEx(&cfg, tc_nt_kernel<BATCHED, PAIR, FP4>, ma, mb, prm);
+    return cudaLaunchKernelEx(&cfg, tc_nt_kernel<BATCHED, PAIR, FP4, LEVEL>, ma, mb, prm);
+}
+
+// CTA pairs of the in-kernel-level kernel (e2m1) that can be resident at once.
+int level_slots() {
+    static int slots[MAX_DEVICES];
+    static bool done[MAX_DEVICES] = {false};
+    const int d = current_device();
+    if (d < 0 || d >= MAX_DEVICES) return 0;
+    if (set_smem_attr<false, true, true, true>() != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!done[d]) {
+        cudaLaunchAttribute at[1];
+        const cudaLaunchConfig_t cfg =
+            pair_config((unsigned)sm_count(), Lay<true, true, true>::SMEM_BYTES, at);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, tc_nt_kernel<false, true, true, true>, &cfg) !=
+            cudaSuccess) {
+            (void)cudaGetLastError();
+            n = 0;
+        }
+        slots[d] = n;
+        done[d] = true;
+    }
+    return slots[d];
 }
 
 Spread spread_factors() {
@@ -1219,6 +1415,67 @@ bmm_status run_tc_strided(int op, int path, const uint64_t* A, int64_t lda, int6
     const cudaError_t e = fp4    ? launch_tc<false, true, true>(ma, mb, prm, units, s)
                           : pair ? launch_tc<false, true, false>(ma, mb, prm, units, s)
                                  : launch_tc<false, false, false>(ma, mb, prm, units, s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return BMM_OK;
+}
+
+// The binary product of each block of a batch through one Strassen level run
+// inside the e2m1 SM-pair kernel: block h is C (m x n, pitch ldc) = A (m x k,
+// pitch lda) times Bt (n x k, pitch ldb)^T at A + h strideA, Bt + h strideB,
+// C + h strideC (words). m and n even, k a multiple of 2 x 512 bits (every
+// quadrant's k whole packed stages, so no copy reads into the neighbouring
+// quadrant), even pitches and strides.
+bmm_status run_tc_level(const uint64_t* A, int64_t lda, int64_t strideA, const uint64_t* Bt,
+                        int64_t ldb, int64_t strideB, uint64_t* C, int64_t ldc, int64_t strideC,
+                        int64_t count, int64_t m, int64_t k, int64_t n, const LevelMasks& masks,
+                        cudaStream_t s) {
+    using LY = Lay<true, true, true>;
+    if (!tc_path_available()) return BMM_ERR_UNSUPPORTED;
+    if (m % 2 || n % 2 || k % (2 * LY::KP) || (lda & 1) || (ldb & 1) ||
+        (count > 1 && ((strideA & 1) || (strideB & 1))))
+        return BMM_ERR_UNSUPPORTED;
+    if (m <= 0 || n <= 0 || k <= 0 || count <= 0) return BMM_OK;
+    if (m > 0x7fffffffLL || n > 0x7fffffffLL || k / KS_MIN > 0x3fffffffLL)
+        return BMM_ERR_UNSUPPORTED;
+    const int slots = level_slots();
+    if (slots <= 0) return BMM_ERR_UNSUPPORTED;
+    uint32_t* err = device_error_word();
+    if (!err) return BMM_ERR_NOMEM;
+    const int64_t hm = m / 2, hk = k / 2, hn = n / 2;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, k / 64, m, lda, count, strideA, BM, LY::KP / 64) ||
+        !make_map(&mb, Bt, k / 64, n, ldb, count, strideB, LY::BROWS, LY::KP / 64))
+        return BMM_ERR_CUDA;
+    Params prm{};
+    prm.C = C;
+    prm.ldc = ldc;
+    prm.strideC = strideC;
+    prm.m = (int)hm;
+    prm.n = (int)hn;
+    prm.nks = (int)(hk / LY::KP) * SUB;
+    prm.op = OP_GF2;
+    prm.kchunk = tc_kchunk_stages(BMM_PATH_TC_FP4_PAIR, prm.nks);
+    prm.tiles_m = (int)((hm + LY::TILE_M - 1) / LY::TILE_M);
+    prm.tiles_n = (int)((hn + BN - 1) / BN);
+    const int64_t total = (int64_t)prm.tiles_m * prm.tiles_n * count;
+    if (total > 0x7fffffff / 7) return BMM_ERR_UNSUPPORTED;
+    prm.total_tiles = (int)total;
+    prm.err = err;
+    prm.sp = spread_factors();
+    for (int h = 0; h < 7; h++) {
+        // a packed stage holds at most QTILES quadrant tiles (every variant's
+        // products combine at most six)
+        if (__builtin_popcount(masks.xi[h] & 0xFu) + __builtin_popcount(masks.eta[h] & 0xFu) >
+            LY::QTILES)
+            return BMM_ERR_UNSUPPORTED;
+        prm.xi4 |= (masks.xi[h] & 0xFu) << (4 * h);
+        prm.eta4 |= (masks.eta[h] & 0xFu) << (4 * h);
+    }
+    for (int q = 0; q < 4; q++) prm.zeta7 |= (masks.zeta[q] & 0x7Fu) << (7 * q);
+    prm.qkw = (int)(hk / 64);
+    TraceScope ts(BMM_PHASE_BASE, s);
+    const int units = prm.total_tiles < slots ? prm.total_tiles : slots;
+    const cudaError_t e = launch_tc<false, true, true, true>(ma, mb, prm, units, s);
     if (e != cudaSuccess) return cuda_fail(e);
     return BMM_OK;
 }

@@ -283,9 +283,47 @@ def test_kernel_level_degenerate_and_unsupported():
     check(run(bmm.GF2, A, eye, m, k, n, depth=1, path=bmm.PATH_POPC, kernel_level=1), A,
           "kernel level, A I")
     if bmm.device_supported():
-        for path in bmm.TENSOR_PATHS:
+        for path in (bmm.PATH_TC_FP8, bmm.PATH_TC_FP8_PAIR):
             with pytest.raises(bmm.BmmError):
                 run(bmm.GF2, ones, ones, m, k, n, depth=2, path=path, kernel_level=1)
+        got = run(bmm.GF2, ones, ones, m, k, n, depth=2, path=bmm.PATH_TC_FP4_PAIR,
+                  kernel_level=1)
+        check(got, want, "tensor kernel level, all ones")
+        check(run(bmm.GF2, A, eye, m, k, n, depth=1, path=bmm.PATH_TC_FP4_PAIR,
+                  kernel_level=1), A, "tensor kernel level, A I")
+
+
+# The innermost level inside the e2m1 tensor kernel: quadrants of (320, kq,
+# 448) bits, ragged in the 256-row and 256-column tiles; kq = 576 is padded to
+# 1024 (two 512-bit packed stages, the second partly zero), kq = 1024 needs
+# no padding; the depth-first and breadth-first splits above it as for the
+# CUDA-core form.
+@pytest.mark.parametrize("kq", [576, 1024])
+@pytest.mark.parametrize("variant", [bmm.WINOGRAD, bmm.SELF_INVERSE, bmm.CHAINING])
+@pytest.mark.parametrize("depth,serial", [(1, 0), (2, 0), (2, 1), (3, 1), (3, 2)])
+def test_kernel_level_tensor(variant, depth, serial, kq):
+    if not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    m, k, n = 320 << depth, kq << depth, 448 << depth
+    Ah, Bh = gen(m, k, 61, 0), gen(k, n, 61, 1)
+    want = O.cubic(O.GF2, Ah, Bh, m, k, n)
+    info = bmm.plan(bmm.GF2, m, k, n, depth=depth, serial=serial, variant=variant,
+                    path=bmm.PATH_TC_FP4_PAIR, kernel_level=1)
+    assert info["kernel_level"] == 1 and info["serial_depth"] == serial
+    got = run(bmm.GF2, Ah, Bh, m, k, n, depth=depth, serial=serial, variant=variant,
+              path=bmm.PATH_TC_FP4_PAIR, kernel_level=1)
+    check(got, want, f"tensor kernel level v={variant} d={depth} s={serial} kq={kq}")
+
+
+def test_kernel_level_tensor_long_k():
+    """Quadrants of 4096 bits of k (eight packed stages per product)."""
+    m, k, n = 512, 8192, 768
+    if not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    Ah, Bh = gen(m, k, 67, 0), gen(k, n, 67, 1)
+    want = O.cubic(O.GF2, Ah, Bh, m, k, n)
+    got = run(bmm.GF2, Ah, Bh, m, k, n, depth=1, path=bmm.PATH_TC_FP4_PAIR, kernel_level=1)
+    check(got, want, "tensor kernel level, long k")
 
 
 @pytest.mark.parametrize("path", paths())

@@ -131,10 +131,11 @@ def parse():
                          "one timed product each) the default workload adds at N = 1")
     ap.add_argument("--kernel-level", type=int, default=0, choices=[0, 1],
                     help="GF(2): run the innermost Strassen level inside the base-case kernel "
-                         "(CUDA-core path)")
+                         "(CUDA-core or e2m1 tensor path)")
     args = ap.parse_args()
-    if args.kernel_level and args.path != "popc":
-        ap.error("--kernel-level 1 runs on the CUDA-core kernel: add --path popc")
+    if args.kernel_level and args.path not in ("popc", "fp4pair"):
+        ap.error("--kernel-level 1 runs on the CUDA-core or the e2m1 kernel: add --path popc "
+                 "or --path fp4pair")
     return args
 
 

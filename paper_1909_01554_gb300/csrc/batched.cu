@@ -607,10 +607,12 @@ bmm_status model_for(int tc_path, Model* out) {
     std::lock_guard<std::mutex> lk(g_model_mu);
     if (!have[d][tc_path]) {
         Model M;
-        const bmm_status st = measure_model(tc_path, &M);
-        if (st != BMM_OK) {
+        if (measure_model(tc_path, &M) != BMM_OK) {
+            // no room or no time to measure now: decide with the built-in
+            // figures (reported as not measured) and measure on a later plan
             (void)cudaGetLastError();
-            return st;
+            *out = default_model(tc_path);
+            return BMM_OK;
         }
         cache[d][tc_path] = M;
         have[d][tc_path] = true;

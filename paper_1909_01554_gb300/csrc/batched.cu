@@ -267,6 +267,11 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
                 w.tn = b;
                 w.nks = (int32_t)c.nks;
                 w.n128 = (c.n128 && b == tn_n - 1) ? 1 : 0;
+                w.op = P->op[i];
+                w.m = (int32_t)P->m[i];
+                w.n = (int32_t)P->n[i];
+                w.C = P->C[i];
+                w.ldc = P->n[i] / 64;
                 items.push_back(w);
                 tile_cost.push_back(c.nks * (w.n128 ? M.tc_stage128 : M.tc_stage) + M.tc_tile);
                 P->tc_tiles++;

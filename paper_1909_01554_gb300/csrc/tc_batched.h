@@ -21,12 +21,16 @@ struct TcProblem {
 
 // One output tile (TC_TILE_M rows, or 2 * TC_TILE_M for an SM pair, x
 // TC_TILE_N columns) of one problem; tm counts tiles of that height.
+// It repeats the problem fields the epilogue needs, so a role reads one item
+// per tile rather than an item and then its problem.
 struct TcWorkItem {
     int32_t prob, tm, tn;
-    int32_t nks;   // the problem's k stages (read without the problem table); may be odd:
-                   // the last packed stage then runs only its first operand stage's MMAs
+    int32_t nks;   // the problem's k stages; may be odd: the last packed stage
+                   // then runs only its first operand stage's MMAs
     int32_t n128;  // 1: the tile's MMAs are N = 128 (its columns past 128 lie beyond n)
-    int32_t pad[3];
+    int32_t op, m, n;
+    uint64_t* C;
+    int64_t ldc;
 };
 
 constexpr int TC_TILE_M = 128;

@@ -152,8 +152,10 @@ struct Lay {
     // accumulator loads need
     static constexpr int QOUT_BYTES = LEVEL ? EPI_WARPS * 32 * 16 * 4 : 0;
     static constexpr int OFF_QOUT = LEVEL ? OFF_PA + PSTAGES * PSTAGE_BYTES : 0;
-    static constexpr int OFF_BAR =
-        LEVEL ? OFF_QOUT + QOUT_BYTES : OFF_PB + PSTAGES * PB_BYTES;
+    // batched: two work items per epilogue warp, fetched a tile ahead
+    static constexpr int OFF_ITEMS = LEVEL ? OFF_QOUT + QOUT_BYTES : OFF_PB + PSTAGES * PB_BYTES;
+    static constexpr int ITEM_BYTES = 48;
+    static constexpr int OFF_BAR = OFF_ITEMS + EPI_WARPS * 2 * ITEM_BYTES;
     static constexpr int OFF_TMEM_SLOT = OFF_BAR + NBARS * 8;
     static constexpr int SMEM_BYTES = OFF_TMEM_SLOT + 16 + 1024;  // + alignment slack
     static_assert(EB_BYTES % 1024 == 0, "swizzle atoms stay 1024-byte aligned");
@@ -578,21 +580,51 @@ __device__ __forceinline__ int tile_count(const Params& p) {
     return c;
 }
 
+// A batched tile from its work item.
+__device__ __forceinline__ Tile tile_of_item(const Params& p, const TcWorkItem& w) {
+    Tile t;
+    const TcProblem* d = p.probs + w.prob;
+    t.ma = &d->mapA;
+    t.mb = &d->mapB;
+    t.C = w.C;
+    t.ldc = w.ldc;
+    t.m = w.m;
+    t.n = w.n;
+    t.nks = w.nks;
+    t.op = w.op;
+    t.tm = w.tm;
+    t.tn = w.tn;
+    t.leaf = 0;
+    t.n128 = w.n128;
+    return t;
+}
+
+// 16 bytes global -> shared, asynchronous (cp.async; wait with cp_async_wait_all).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// items: batched, this unit's slice of the work list (read once per kernel,
+// so that fetching a tile's item is one load, not two dependent ones).
 template <bool BATCHED, bool PAIR>
-__device__ __forceinline__ Tile tile_get(const Params& p, int idx, const CUtensorMap* tmA,
-                                         const CUtensorMap* tmB) {
+__device__ __forceinline__ Tile tile_get(const Params& p, const TcWorkItem* items, int idx,
+                                         const CUtensorMap* tmA, const CUtensorMap* tmB) {
     Tile t;
     if (BATCHED) {
-        const TcWorkItem w = p.items[p.cta_ptr[unit_id<PAIR>()] + idx];
+        const TcWorkItem w = items[idx];
         const TcProblem* d = p.probs + w.prob;
         t.ma = &d->mapA;
         t.mb = &d->mapB;
-        t.C = d->C;
-        t.ldc = d->ldc;
-        t.m = d->m;
-        t.n = d->n;
+        t.C = w.C;
+        t.ldc = w.ldc;
+        t.m = w.m;
+        t.n = w.n;
         t.nks = w.nks;
-        t.op = d->op;
+        t.op = w.op;
         t.tm = w.tm;
         t.tn = w.tn;
         t.leaf = 0;
@@ -620,10 +652,10 @@ __device__ __forceinline__ Tile tile_get(const Params& p, int idx, const CUtenso
 struct TileK {
     int nks, n128;
 };
-template <bool BATCHED, bool PAIR>
-__device__ __forceinline__ TileK tile_k(const Params& p, int idx) {
+template <bool BATCHED>
+__device__ __forceinline__ TileK tile_k(const Params& p, const TcWorkItem* items, int idx) {
     if (BATCHED) {
-        const TcWorkItem* w = p.items + p.cta_ptr[unit_id<PAIR>()] + idx;
+        const TcWorkItem* w = items + idx;
         return {w->nks, w->n128};
     }
     return {p.nks, 0};
@@ -709,6 +741,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     const int kchunk = p.kchunk;
     const int my_tiles = tile_count<BATCHED, PAIR>(p);
+    const TcWorkItem* my_items = BATCHED ? p.items + p.cta_ptr[unit_id<PAIR>()] : nullptr;
     int total_pit = 0;  // packed stages this CTA runs (batched: from the plan)
     if (BATCHED)
         total_pit = p.cta_ptr[unit_count<PAIR>() + 1 + unit_id<PAIR>()];
@@ -727,8 +760,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             // Batched: a tile's work item is read two tiles ahead and its
             // TMA maps prefetched one tile ahead, so neither the item load
             // nor a map fetch stalls the copies of the tile before it.
-            Tile nxt = my_tiles > 0 ? tile_get<BATCHED, PAIR>(p, 0, &tmA, &tmB) : Tile{};
-            Tile nxt2 = my_tiles > 1 ? tile_get<BATCHED, PAIR>(p, 1, &tmA, &tmB) : nxt;
+            Tile nxt = my_tiles > 0 ? tile_get<BATCHED, PAIR>(p, my_items, 0, &tmA, &tmB) : Tile{};
+            Tile nxt2 = my_tiles > 1 ? tile_get<BATCHED, PAIR>(p, my_items, 1, &tmA, &tmB) : nxt;
             if (BATCHED && my_tiles > 0) {
                 prefetch_tensormap(nxt.ma);
                 prefetch_tensormap(nxt.mb);
@@ -740,7 +773,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                     prefetch_tensormap(nxt.ma);
                     prefetch_tensormap(nxt.mb);
                 }
-                if (i + 2 < my_tiles) nxt2 = tile_get<BATCHED, PAIR>(p, i + 2, &tmA, &tmB);
+                if (i + 2 < my_tiles)
+                    nxt2 = tile_get<BATCHED, PAIR>(p, my_items, i + 2, &tmA, &tmB);
                 const int arow = tc.tm * LY::TILE_M + (int)rank * BM;
                 // an N = 128 tile takes 64 of its columns from each CTA of a pair
                 const int brow =
@@ -987,14 +1021,17 @@ __global__ void __launch_bounds__(THREADS, 1)
             bool ok = true;
             // a tile's k stages are loaded one tile ahead (batched: from the
             // work list in global memory, off the issue path)
-            TileK tk_next = my_tiles > 0 ? tile_k<BATCHED, PAIR>(p, 0) : TileK{0, 0};
+            // (batched: items read two tiles ahead of their use)
+            TileK tk_next = my_tiles > 0 ? tile_k<BATCHED>(p, my_items, 0) : TileK{0, 0};
+            TileK tk_next2 = my_tiles > 1 ? tile_k<BATCHED>(p, my_items, 1) : tk_next;
             // LEVEL: every tile position runs seven products, each an
             // accumulator tile of its own
             const int mma_tiles = LEVEL ? 7 * my_tiles : my_tiles;
             for (int i = 0; ok && i < mma_tiles; i++) {
                 const int nks = tk_next.nks;
                 const uint32_t id = BATCHED && tk_next.n128 ? idesc128 : idesc;
-                if (i + 1 < mma_tiles) tk_next = tile_k<BATCHED, PAIR>(p, i + 1);
+                tk_next = tk_next2;
+                if (i + 2 < mma_tiles) tk_next2 = tile_k<BATCHED>(p, my_items, i + 2);
                 int kin = 0;
                 for (int ks = 0; ks < nks; ks += SUB, pit++) {
                     // Every producer fills the slots in order, so one wait on
@@ -1068,8 +1105,30 @@ __global__ void __launch_bounds__(THREADS, 1)
         constexpr int CW = BN / (EPI_WARPS / 4) / 32;  // 32-column chunks per warp
         int seg = 0;
         bool ok = true;
+        // batched: each tile's work item is copied into this warp's shared
+        // slot while the tile before it runs, off the accumulator hand-off path
+        const uint32_t islot =
+            sbase + (uint32_t)(LY::OFF_ITEMS + (warp - EPI_WARP0) * 2 * LY::ITEM_BYTES);
+        static_assert(sizeof(TcWorkItem) == LY::ITEM_BYTES, "three 16-byte copies per item");
+        auto fetch_item = [&](int idx) {
+            if (lane < 3)
+                cp_async16(islot + (uint32_t)((idx & 1) * LY::ITEM_BYTES + 16 * lane),
+                           reinterpret_cast<const uint8_t*>(my_items + idx) + 16 * lane);
+        };
+        if (BATCHED && my_tiles > 0) fetch_item(0);
         for (int i = 0; ok && i < my_tiles; i++) {
-            const Tile tc = tile_get<BATCHED, PAIR>(p, i, &tmA, &tmB);
+            Tile tc;
+            if (BATCHED) {
+                cp_async_wait_all();
+                __syncwarp();
+                TcWorkItem w;
+                std::memcpy(&w, smem + (islot - sbase) + (i & 1) * LY::ITEM_BYTES, sizeof(w));
+                __syncwarp();
+                if (i + 1 < my_tiles) fetch_item(i + 1);
+                tc = tile_of_item(p, w);
+            } else {
+                tc = tile_get<BATCHED, PAIR>(p, my_items, i, &tmA, &tmB);
+            }
             const int nseg = (tc.nks + kchunk - 1) / kchunk;
             const bool gf2 = tc.op == OP_GF2;
             // an N = 128 tile writes no accumulator column past 128: the warps

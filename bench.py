@@ -1079,7 +1079,8 @@ def run_batched(args):
                        "shapes": "m, k, n log-uniform in [256, 8192], multiples of 64",
                        "ops": "50/50 GF(2) (p=1/2) / Boolean (p=1/sqrt(k))",
                        "sum_2mkn": bops_step, "launch": "one CUDA-graph replay of a batch plan "
-                       "(batched transpose, row padding, persistent tcgen05 base case)",
+                       "(batched transpose, row padding, persistent tcgen05 base case; a "
+                       "persistent CUDA-core launch for problems the plan sends there)",
                        "l2": "inputs larger than L2 (~4 GB per step)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -970,14 +970,16 @@ def run_batched(args):
 
     # the base-case kernels alone, timed with events on their stream (one
     # plan run; the best of three)
-    base_ms = None
+    base_ms = pre_ms = None
     for _ in range(3):
         bmm.trace_enable(True)
         plan.run(stream=sh)
         torch.cuda.synchronize()
         bmm.trace_enable(False)
         base_n, t = bmm.trace_read(bmm.PHASE_BASE)
+        _, tp = bmm.trace_read(bmm.PHASE_TRANSPOSE)  # batched transpose and row padding
         base_ms = t if base_ms is None else min(base_ms, t)
+        pre_ms = tp if pre_ms is None else min(pre_ms, tp)
     pk, pk_kind = peaks()
     fp4 = plan.path() == bmm.PATH_TC_FP4_PAIR
     peak, peak_source = tensor_peak(pk, pk_kind, fp4)
@@ -999,6 +1001,7 @@ def run_batched(args):
         "strassen_depths": sorted({c["strassen_depth"] for c in choices}),
         "macs_issued_over_needed": pst["macs_issued"] / pst["macs_needed"],
         "model_est_base_ms": pst["est_ms"], "measured_base_ms": base_ms,
+        "transpose_and_pad_ms": pre_ms,
         "model": {k_: v for k_, v in bmodel.items() if k_ != "path"},
     }
 

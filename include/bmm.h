@@ -195,11 +195,12 @@ bmm_status bmm_bool_batched(int32_t count, const uint64_t *const *A, const uint6
  * per problem, the tensor tile work list and its assignment to SM pairs
  * (longest first onto the least loaded pair, by model cost), the CUDA-core
  * tile list, and scratch for the transposed B's; it allocates device memory
- * and copies to it synchronously. run launches on `stream` a batched
- * transpose, row padding for tensor problems with k/64 odd, one persistent
- * tensor-core launch and, when some problem chose the CUDA cores, one
- * persistent CUDA-core launch; it allocates nothing and does not
- * synchronise, and it reads the matrices named at create time, so new data
+ * and copies to it synchronously. run launches on `stream` the batched
+ * transposes of every B (a TMA launch for those whose row pitches are even,
+ * a load/store launch for the rest), row padding for tensor problems with
+ * k/64 odd, one persistent tensor-core launch and, when some problem chose
+ * the CUDA cores, one persistent CUDA-core launch; it allocates nothing and
+ * does not synchronise, and it reads the matrices named at create time, so new data
  * in the same buffers needs no new plan. destroy frees the plan; call it
  * only after the runs have completed. */
 typedef struct bmm_batched_plan_s *bmm_batched_plan;
@@ -330,7 +331,10 @@ bmm_status bmm_bool_host(const uint64_t *A, const uint64_t *B, uint64_t *C, int6
 /* ---- the steps of the path, exported for tests and experiments ---------- */
 
 /* Bit transpose: Xt (cols x rows) = X^T (X is rows x cols). The paper
- * transposes the right operand so both operands run along k (Sec. 3.5). */
+ * transposes the right operand so both operands run along k (Sec. 3.5).
+ * Tiles of 512 x 512 bits move through shared memory by TMA where both row
+ * pitches are even and the matrix has a whole tile a side, else by loads and
+ * stores. */
 bmm_status bmm_transpose(const uint64_t *X, uint64_t *Xt, int64_t rows, int64_t cols,
                          bmm_stream_t stream);
 

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libbmm.so.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -56,9 +57,19 @@ inline bool is_tc_path(int path) {
            path == BMM_PATH_TC_FP4_PAIR;
 }
 
+// A 2-D TMA map over uint64 words (words x rows, row stride in bytes, a
+// multiple of 16), box of box_words x box_rows, optionally 64-byte swizzled.
+// False if the driver's encoder is unavailable or refuses the arguments.
+bool make_map_2d(CUtensorMap* map, const void* base, int64_t words, int64_t rows,
+                 int64_t stride_bytes, int box_words, int box_rows, bool swizzle64);
+
 // ---- launchers (each returns a launch error, or cudaSuccess) -------------
 cudaError_t launch_transpose(const uint64_t* X, uint64_t* Xt, int64_t rows, int64_t cols,
                              cudaStream_t s);
+// Always the load/store form, which needs no device memory of the library's
+// own (the TMA form records bounded-wait timeouts in the device error word).
+cudaError_t launch_transpose_loadstore(const uint64_t* X, uint64_t* Xt, int64_t rows,
+                                       int64_t cols, cudaStream_t s);
 // X is rows x cols with row pitch `pitch` words; Xt is cols x rows, row pitch tpitch words.
 cudaError_t launch_transpose_pitched(const uint64_t* X, int64_t pitch, uint64_t* Xt,
                                      int64_t tpitch, int64_t rows, int64_t cols,
@@ -72,6 +83,18 @@ struct TransposeJob {
 };
 // CTA tiles one transpose takes (the batched launch needs their prefix sums).
 int64_t transpose_tiles(int64_t rows, int64_t cols);
+// A transpose of a batch in its TMA form (device memory, aligned as its maps).
+struct TmaTransposeJob {
+    CUtensorMap mx, mt;  // X (words x rows) and Xt (words x cols), 64-byte swizzled boxes
+    int64_t gx, cols;    // tiles along X's words; Xt's rows
+};
+// Fills the TMA form of a job; false where it does not apply (odd pitches,
+// unaligned bases, less than a 512 x 512 tile a side, no TMA on the device):
+// such a job goes to launch_transpose_batched.
+bool make_transpose_tma_job(TmaTransposeJob* out, const TransposeJob& j);
+// All TMA-form jobs in one launch; first[i] = tiles of jobs 0..i-1 (device).
+cudaError_t launch_transpose_tma_batched(const TmaTransposeJob* jobs, const int64_t* first,
+                                         int count, int64_t total_tiles, cudaStream_t s);
 // All jobs in one launch; first[i] = tiles of jobs 0..i-1 (device arrays).
 cudaError_t launch_transpose_batched(const TransposeJob* jobs, const int64_t* first, int count,
                                      int64_t total_tiles, cudaStream_t s);

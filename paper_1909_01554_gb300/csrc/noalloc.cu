@@ -54,7 +54,7 @@ extern "C" bmm_status bmm_product_noalloc(int32_t op, const uint64_t* A, const u
     const cudaStream_t s = (cudaStream_t)stream;
     // The transpose writes every word of B^T that the product reads, so the
     // array needs no clearing between calls.
-    cudaError_t e = launch_transpose(B, Bt, k, n, s);
+    cudaError_t e = launch_transpose_loadstore(B, Bt, k, n, s);
     if (e != cudaSuccess) return cuda_fail(e);
     e = launch_popc_nt(op, A, k / 64, 0, Bt, k / 64, 0, C, n / 64, 0, 1, m, k, n, s);
     if (e != cudaSuccess) return cuda_fail(e);

@@ -1288,6 +1288,28 @@ bool make_map(CUtensorMap* map, const uint64_t* base, int64_t kwords, int64_t ro
     return r == CUDA_SUCCESS;
 }
 
+}  // namespace
+
+// 2-D map over uint64 words (inner words, outer rows, row stride in bytes),
+// box (box_words, box_rows), 64-byte swizzle when asked (box rows of 64 B).
+bool make_map_2d(CUtensorMap* map, const void* base, int64_t words, int64_t rows,
+                 int64_t stride_bytes, int box_words, int box_rows, bool swizzle64) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)words, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)stride_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)box_words, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r =
+        fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE,
+           swizzle64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+namespace {
+
 constexpr int MAX_DEVICES = 64;
 
 int current_device() {

@@ -42,7 +42,11 @@ def check(got, want, what):
 
 
 # ------------------------------------------------------------ transpose
-@pytest.mark.parametrize("rows,cols", [(64, 64), (256, 512), (320, 192), (4096, 128), (64, 1344)])
+# The last three shapes take the TMA form (both pitches even, at least one
+# 512 x 512 tile), with tiles ragged in both directions; the first five the
+# load/store form (odd pitches or less than a tile a side).
+@pytest.mark.parametrize("rows,cols", [(64, 64), (256, 512), (320, 192), (4096, 128), (64, 1344),
+                                       (512, 512), (1664, 640), (1152, 2048)])
 def test_transpose(rows, cols):
     X = gen(rows, cols, 3, 0)
     dX = to_dev(X)

@@ -69,9 +69,9 @@ FP4_MAC_PER_SM_CLK = 16384
 # (GF(2) depth 3 with one depth-first level: 7 leaf launches + 1 Boolean).
 TRAFFIC_RECORD = {
     "kernel": "paper_1909_01554_gb300/csrc/tc_gemm.cu",
-    "sha256": "810229f441732f46e02577ed858e817c8ac75f65962c9664880c002a8add0680",
+    "sha256": "d015b9d746341926915a55cbc4072d3e4ca887e0201cbef8a85b60a9a5f1eef3",
     "workload": "square32768", "gf2_depth": 3, "gf2_serial": 1, "base_launches": 8,
-    "dram_bytes_per_step": 2782602752,
+    "dram_bytes_per_step": 2781064192,
 }
 
 

@@ -727,7 +727,11 @@ bmm_status plan_create(int32_t count, const int32_t* ops, const uint64_t* const*
             return BMM_ERR_INVALID;
         if (is_tc_path(path)) tcp = path;
     }
-    const bool all_popc = !paths && path == BMM_PATH_POPC;
+    bool all_popc = !paths && path == BMM_PATH_POPC;
+    if (paths) {
+        all_popc = true;
+        for (int i = 0; i < count; i++) all_popc = all_popc && paths[i] == BMM_PATH_POPC;
+    }
     if (tcp == BMM_PATH_AUTO) tcp = all_popc ? BMM_PATH_POPC : auto_path();
     if (is_tc_path(tcp)) {
         if (!tc_path_available()) return BMM_ERR_UNSUPPORTED;
@@ -752,6 +756,13 @@ bmm_status plan_create(int32_t count, const int32_t* ops, const uint64_t* const*
     if (st == BMM_OK) {
         decide(P, req.data());
         st = plan_build(P);
+    }
+    // what the first run would otherwise set up (the device error word, the
+    // kernel attributes), so that even a plan's first run can be captured
+    if (st == BMM_OK && count > 0 && !device_error_word()) st = BMM_ERR_NOMEM;
+    if (st == BMM_OK && P->grid > 0) {
+        const cudaError_t e = tc_prepare_batched(P->pair, P->fp4);
+        if (e != cudaSuccess) st = cuda_fail(e);
     }
     if (st != BMM_OK) {
         plan_free(P);

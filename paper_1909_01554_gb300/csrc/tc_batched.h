@@ -46,6 +46,10 @@ bool tc_make_problem(TcProblem* out, const uint64_t* A, int64_t lda, const uint6
                      int64_t ldb, uint64_t* C, int64_t ldc, int64_t m, int64_t k, int64_t n,
                      int op, bool pair, bool fp4);
 
+// The batched kernel's one-time launch setup on the current device (done
+// when a plan is made, so that a plan's first run can be captured).
+cudaError_t tc_prepare_batched(bool pair, bool fp4);
+
 // One persistent launch over the per-unit work lists; a unit is one CTA, or
 // one CTA pair when `pair`. unit_ptr has 2 * (units + 1) entries: the first
 // units + 1 delimit each unit's items, entry units + 1 + u is unit u's

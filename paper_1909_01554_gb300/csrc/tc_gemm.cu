@@ -1592,6 +1592,13 @@ int tc_problem_kchunk(bool fp4) {
     return tc_kchunk_stages(fp4 ? BMM_PATH_TC_FP4_PAIR : BMM_PATH_TC_FP8, 0x7fffffff);
 }
 
+cudaError_t tc_prepare_batched(bool pair, bool fp4) {
+    if (fp4 && !pair) return cudaErrorInvalidValue;
+    return fp4    ? set_smem_attr<true, true, true>()
+           : pair ? set_smem_attr<true, true, false>()
+                  : set_smem_attr<true, false, false>();
+}
+
 cudaError_t tc_launch_batched(const TcProblem* d_probs, const TcWorkItem* d_items,
                               const int32_t* d_unit_ptr, int units, bool pair, bool fp4,
                               cudaStream_t s) {

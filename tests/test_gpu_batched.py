@@ -260,3 +260,27 @@ def test_batched_config5_shapes_sampled():
                 Ar = bitgen.fill_cpu(m, k, seed, 0, p=p, row0=r, nrows=1)
                 want = O.rows(o, Ar, B, k, n)
                 assert (got[r] == want[0]).all(), f"problem {i} row {r}"
+
+
+def test_plan_first_run_captured_in_a_graph():
+    """A plan whose very first run is captured in a CUDA graph (everything a
+    run needs is set up when the plan is made), with problems on both base
+    cases, then replayed: exact."""
+    if not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    shapes = SMALL + [(1024, 1024, 1024, 0), (512, 2048, 768, 1)]
+    req = [bmm.PATH_POPC if i % 3 == 0 else bmm.PATH_AUTO for i in range(len(shapes))]
+    host, dev = make_batch(shapes, 71)
+    plan = bmm.BatchedPlan([s[3] for s in shapes], [d[0] for d in dev], [d[1] for d in dev],
+                           [d[2] for d in dev], [s[0] for s in shapes], [s[1] for s in shapes],
+                           [s[2] for s in shapes], paths=req)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    bmm.stream_status()
+    check_all(shapes, host, dev)
+    plan.destroy()

@@ -436,8 +436,9 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
     P->tma_total = ttfirst.back();
     P->pad_count = pads;
     P->pad_total = pfirst.back();
-    BMM_CUDA_TRY(cudaMemcpy(P->d_probs, probs.data(), sizeof(TcProblem) * count,
-                            cudaMemcpyHostToDevice));
+    if (count > 0)
+        BMM_CUDA_TRY(cudaMemcpy(P->d_probs, probs.data(), sizeof(TcProblem) * count,
+                                cudaMemcpyHostToDevice));
     if (!flat.empty())
         BMM_CUDA_TRY(cudaMemcpy(P->d_items, flat.data(), sizeof(TcWorkItem) * flat.size(),
                                 cudaMemcpyHostToDevice));
@@ -461,8 +462,9 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
         BMM_CUDA_TRY(cudaMemcpy(P->d_pfirst, pfirst.data(), sizeof(int64_t) * pads,
                                 cudaMemcpyHostToDevice));
     }
-    BMM_CUDA_TRY(cudaMemcpy(P->d_pcjobs, pcjobs.data(), sizeof(PopcJob) * count,
-                            cudaMemcpyHostToDevice));
+    if (count > 0)
+        BMM_CUDA_TRY(cudaMemcpy(P->d_pcjobs, pcjobs.data(), sizeof(PopcJob) * count,
+                                cudaMemcpyHostToDevice));
     if (!pflat.empty())
         BMM_CUDA_TRY(cudaMemcpy(P->d_pctiles, pflat.data(), sizeof(PopcTile) * pflat.size(),
                                 cudaMemcpyHostToDevice));

@@ -284,3 +284,19 @@ def test_plan_first_run_captured_in_a_graph():
     bmm.stream_status()
     check_all(shapes, host, dev)
     plan.destroy()
+
+
+def test_empty_batch_plan():
+    """A plan over no problems builds, runs (launching nothing) and frees."""
+    L = bmm.lib()
+    import ctypes
+
+    h = ctypes.c_void_p(0)
+    assert L.bmm_batched_plan_create(0, None, None, None, None, None, None, None,
+                                     ctypes.byref(h)) == bmm.OK
+    l0 = bmm.launch_count()
+    assert L.bmm_batched_plan_run(h, None) == bmm.OK
+    assert bmm.launch_count() == l0
+    st = bmm.BatchedStats()
+    assert L.bmm_batched_plan_stats(h, ctypes.byref(st)) == bmm.OK and st.problems == 0
+    assert L.bmm_batched_plan_destroy(h) == bmm.OK

@@ -205,3 +205,26 @@ def test_cached_buffers_across_calls_and_release():
         got = host_product(op, Ah, Bh, m, k, n, pinned=True, host_depth=hd, device_bytes=1 << 30)
         assert (got == O.cubic(O.GF2, Ah, Bh, m, k, n)).all(), (m, k, n, hd)
     bmm.host_release()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("path", [bmm.PATH_POPC, bmm.PATH_TC_FP4_PAIR])
+def test_gf2_host_level_over_in_kernel_level(path):
+    """A host level above device products whose innermost Strassen level runs
+    inside the base-case kernel, on both paths that have that form; the
+    device estimate follows the padded k of the tensor form."""
+    if not gpu_ok():
+        pytest.skip("no GPU")
+    if path == bmm.PATH_TC_FP4_PAIR and not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    m, k, n = 2048, 2048, 1536
+    kw = dict(path=path, depth=2, kernel_level=1, device_bytes=1 << 30)
+    hp = bmm.host_plan(bmm.GF2, m, k, n, host_depth=1, **kw)
+    dev = bmm.plan(bmm.GF2, hp["sub_m"], hp["sub_k"], hp["sub_n"], path=path, depth=2,
+                   kernel_level=1)
+    assert dev["kernel_level"] == 1
+    bufs = 2 * (hp["sub_m"] * hp["sub_k"] + hp["sub_k"] * hp["sub_n"] + hp["sub_m"] * hp["sub_n"]) // 8
+    assert hp["device_bytes"] == bufs + dev["workspace_bytes"] + (8 << 20)
+    Ah, Bh = gen(m, k, 83, 0), gen(k, n, 83, 1)
+    got = host_product(bmm.GF2, Ah, Bh, m, k, n, pinned=True, host_depth=1, **kw)
+    assert (got == O.cubic(O.GF2, Ah, Bh, m, k, n)).all()

@@ -1242,6 +1242,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                         crow[w0 + c] = (uint64_t)out[0][2 * c] | ((uint64_t)out[0][2 * c + 1] << 32);
             }
         }
+        // a loop left early (a wait gave up) may still have an item copy in
+        // flight into this warp's slot
+        if (BATCHED) cp_async_wait_all();
     }
 
     tc_fence_before();

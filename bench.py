@@ -69,7 +69,7 @@ FP4_MAC_PER_SM_CLK = 16384
 # (GF(2) depth 3 with one depth-first level: 7 leaf launches + 1 Boolean).
 TRAFFIC_RECORD = {
     "kernel": "paper_1909_01554_gb300/csrc/tc_gemm.cu",
-    "sha256": "a35e468dd8c5216d168a407a8071a81cd734ccb2ab42f0ce9465cec5920136f6",
+    "sha256": "ca977e867ceb42cea71dffdae50cae4403355d59c57737e9f8a3bc5846ee2dd2",
     "workload": "square32768", "gf2_depth": 3, "gf2_serial": 1, "base_launches": 8,
     "dram_bytes_per_step": 2781064192,
 }

@@ -52,6 +52,15 @@
 // output word j holds bit 8t + j of the packed word); A and Bt use the same
 // permutation, so the contraction is unchanged.
 //
+// e2m1 form (FP4): every bit becomes a 4-bit e2m1 value under a uniform
+// block scale, twice the k per MMA (kind::mxf4); an operand stage then holds
+// 256 bits of k and a packed stage 512.
+//
+// Batched form (BATCHED): each unit walks its own list of work items, one
+// tile of one problem each (per-problem TMA maps); a tile may run N = 128
+// MMAs (a tail with at most 128 columns inside n) and may end in half a
+// packed stage. Uniform form: the tiles of `count` equal leaves.
+//
 // Every mbarrier wait is bounded (wall clock, ~2 s). A wait that gives up
 // records BMM device error DEVERR_TIMEOUT and makes its role stop; the CTA
 // then drains its own in-flight copies and MMAs (again bounded), frees TMEM

@@ -188,10 +188,15 @@ bmm_status bmm_bool_batched(int32_t count, const uint64_t *const *A, const uint6
  * stage of k and per tile of each kernel, from synthetic batches timed the
  * first time a plan on that device and tensor path needs it (Sec. 3.17:
  * what memory does not fix is chosen by measurement; that first create
- * takes some tens of milliseconds longer). Every problem runs cubic
- * (Strassen depth 0): the planner's depth rule keeps leaves of at least
- * 8192 bits, so it gives depth 0 to every side below 16384, and a batch
- * plan has no XOR passes. It then builds, on the current device, TMA maps
+ * takes some tens of milliseconds longer). A binary problem gets the
+ * Strassen depth a single product of its shape would get (Sec. 3.8: the
+ * rule keeps leaves of at least 8192 bits, so depth 0 for any side below
+ * 16384, or a tuned record for the shape); one with depth > 0 leaves the
+ * batched launches and runs, after them, as its own Strassen product
+ * (transpose, XOR passes, leaves) in scratch that the plan holds, sized for
+ * the largest such problem; an AUTO entry of a plan on the device's
+ * automatic tensor path leaves its path to that single-product planner too.
+ * The rest run cubic in the batched launches. It then builds, on the current device, TMA maps
  * per problem, the tensor tile work list and its assignment to SM pairs
  * (longest first onto the least loaded pair, by model cost), the CUDA-core
  * tile list, and scratch for the transposed B's; it allocates device memory
@@ -199,7 +204,8 @@ bmm_status bmm_bool_batched(int32_t count, const uint64_t *const *A, const uint6
  * transposes of every B (a TMA launch for those whose row pitches are even,
  * a load/store launch for the rest), row padding for tensor problems with
  * k/64 odd, one persistent tensor-core launch and, when some problem chose
- * the CUDA cores, one persistent CUDA-core launch; it allocates nothing and
+ * the CUDA cores, one persistent CUDA-core launch, then the Strassen
+ * problems one after another; it allocates nothing and
  * does not synchronise, and it reads the matrices named at create time, so new data
  * in the same buffers needs no new plan. destroy frees the plan; call it
  * only after the runs have completed. */
@@ -237,13 +243,16 @@ typedef struct {
     int32_t tail_n;         /* columns the MMAs of its last column tile cover (tile_n or 128) */
     int32_t k_step;         /* bits of k per step the tiles run in (k is padded to whole steps) */
     int64_t k_steps;        /* steps of k per tile */
-    int32_t strassen_depth; /* 0: batched problems run cubic */
+    int32_t strassen_depth; /* 0: cubic in the batched launches; > 0: its own
+                               Strassen product (tile fields: its leaves') */
     double est_us;          /* the model's time for all its tiles on one unit (CTA pair or CTA) */
 } bmm_batched_choice;
 bmm_status bmm_batched_plan_choice(bmm_batched_plan plan, int32_t i, bmm_batched_choice *out);
 
-/* Totals of a plan. macs_issued / macs_needed is the padding the tiles
- * carry (MACs computed over sum of m k n). */
+/* Totals of a plan. macs_needed is sum of m k n; macs_issued the MACs the
+ * base case computes: tiles padded to whole tiles and k steps, and for a
+ * Strassen problem 7^d leaves of (m k n) / 8^d. est_ms covers the batched
+ * launches only. */
 typedef struct {
     int32_t problems, tensor_problems, popc_problems;
     int32_t tensor_path;          /* the tensor path the plan uses for tensor problems */
@@ -251,6 +260,8 @@ typedef struct {
     double macs_needed, macs_issued;
     double est_ms;                /* the model's base-case time of one run */
     int32_t model_measured;       /* 1: the model was measured on this device */
+    int32_t strassen_problems;    /* problems run as their own Strassen products
+                                     (counted in tensor_ or popc_problems too) */
 } bmm_batched_stats;
 bmm_status bmm_batched_plan_stats(bmm_batched_plan plan, bmm_batched_stats *out);
 

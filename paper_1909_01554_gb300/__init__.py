@@ -92,7 +92,7 @@ class BatchedStats(ctypes.Structure):
                 ("tensor_tiles", ctypes.c_int64), ("tensor_tiles_n128", ctypes.c_int64),
                 ("popc_tiles", ctypes.c_int64), ("macs_needed", ctypes.c_double),
                 ("macs_issued", ctypes.c_double), ("est_ms", ctypes.c_double),
-                ("model_measured", ctypes.c_int32)]
+                ("model_measured", ctypes.c_int32), ("strassen_problems", ctypes.c_int32)]
 
 
 class BatchedModel(ctypes.Structure):

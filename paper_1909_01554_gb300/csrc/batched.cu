@@ -10,7 +10,10 @@
 //     of its 256 columns lie inside n and the measured N = 128 stage is
 //     cheaper than the N = 256 one;
 //   - k in operand stages (256 bits e2m1, 128 bits e4m3); an odd count ends
-//     in half a packed stage, whose second operand stage is not multiplied.
+//     in half a packed stage, whose second operand stage is not multiplied;
+//   - for a binary product, the Strassen depth a single product of its shape
+//     gets (Sec. 3.8); one with depth > 0 runs as its own Strassen product
+//     after the batched launches, in plan-held scratch.
 // Then it builds per-problem TMA maps over A (or a copy of A with an even row
 // pitch) and over the transposed B, the work list of all tensor tiles
 // (256 x 256 on SM pairs, 128 x 256 where pairs are unavailable) assigned
@@ -20,9 +23,9 @@
 // Running a plan only launches kernels: one batched bit transpose of every B,
 // one pass that pads rows whose k/64 word count is odd (tensor problems), one
 // persistent tensor-core launch over the tensor tiles and, when some problem
-// chose the CUDA cores, one persistent CUDA-core launch over theirs. Nothing
-// in a run allocates or synchronises, so a run can be captured in a CUDA
-// graph and replayed.
+// chose the CUDA cores, one persistent CUDA-core launch over theirs, then
+// the Strassen problems' own launches. Nothing in a run allocates or
+// synchronises, so a run can be captured in a CUDA graph and replayed.
 //
 // The cost model (per device and tensor path, measured once on the first
 // plan that needs it; Sec. 3.17 fixes what memory forces and chooses the
@@ -137,6 +140,8 @@ struct BatchChoice {
     int n128 = 0;              // tensor: the last column tile runs N = 128 MMAs
     int64_t nks = 0;           // tensor: operand stages of k; CUDA cores: 256-bit stages
     double cost_ns = 0.0;      // model time of all its tiles on one unit
+    bool strassen = false;     // runs as its own Strassen product (plan below)
+    Plan sp;                   // that product's plan (depth > 0)
 };
 
 struct bmm_batched_plan_s {
@@ -167,6 +172,8 @@ struct bmm_batched_plan_s {
     int64_t* d_pfirst = nullptr;
     PopcJob* d_pcjobs = nullptr;
     PopcTile* d_pctiles = nullptr;
+    void* strassen_ws = nullptr;  // inside dmem: scratch of the largest Strassen problem
+    int strassen_problems = 0;
     int grid = 0;                 // tensor launch units (0: no tensor problem)
     int64_t pc_tiles = 0;         // CUDA-core tiles (0: no CUDA-core problem)
     int64_t transpose_total = 0, pad_total = 0;
@@ -212,6 +219,28 @@ void decide(bmm_batched_plan_s* P, const int32_t* req) {
                       std::max(1, M.tc_units);
         }
         const int want = req ? req[i] : BMM_PATH_AUTO;
+        // Strassen depth per shape (Sec. 3.8): the single-product planner's
+        // choice (its rule: recurse while every leaf side stays >= 8192 bits,
+        // or a tuned record for the shape); a binary product it gives depth
+        // > 0 runs as its own Strassen product after the persistent launches.
+        // AUTO entries of a plan on the device's automatic tensor path leave
+        // the path to that planner too (a tuned record applies); otherwise
+        // the entry's path, or the plan's tensor path, is fixed.
+        if (P->op[i] == OP_GF2) {
+            bmm_opts o;
+            bmm_opts_default(&o);
+            if (want != BMM_PATH_AUTO)
+                o.path = want;
+            else if (P->tc_path != auto_path())
+                o.path = P->tc_path;
+            Plan sp;
+            if (make_plan(OP_GF2, m, k, n, &o, &sp) == BMM_OK && sp.depth > 0) {
+                c.strassen = true;
+                c.sp = sp;
+                c.path = sp.path;
+                continue;
+            }
+        }
         const bool use_tc = tc && (want == P->tc_path || (want == BMM_PATH_AUTO && tc_cost <= pc_cost));
         if (use_tc) {
             c.path = P->tc_path;
@@ -238,10 +267,29 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
     int pads = 0;
     P->tc_problems = P->pc_problems = 0;
     P->macs_needed = P->macs_issued = 0.0;
+    uint64_t strassen_ws = 0;
+    P->strassen_problems = 0;
     for (int i = 0; i < count; i++) {
         const int64_t kw = P->k[i] / 64;
         const bool tc = P->choice[i].path != BMM_PATH_POPC;
         P->kp[i] = (kw + 1) / 2 * 2;
+        if (P->choice[i].strassen) {
+            // its own plan's passes (transpose, XOR passes, leaves) in a
+            // scratch shared with the other Strassen problems (they run one
+            // after another)
+            const Plan& sp = P->choice[i].sp;
+            strassen_ws = std::max<uint64_t>(strassen_ws, sp.workspace_bytes);
+            P->strassen_problems++;
+            P->macs_needed += (double)P->m[i] * (double)P->k[i] * (double)P->n[i];
+            double leaves = 1.0;
+            for (int l = 0; l < sp.depth; l++) leaves *= 7.0;
+            P->macs_issued += leaves * (double)(sp.m >> sp.depth) * (double)(sp.kp >> sp.depth) *
+                              (double)(sp.n >> sp.depth);
+            P->tc_problems += is_tc_path(sp.path) ? 1 : 0;
+            P->pc_problems += is_tc_path(sp.path) ? 0 : 1;
+            bt_off[i] = 0;
+            continue;
+        }
         bt_off[i] = ws;
         ws += round256((uint64_t)P->n[i] * P->kp[i] * 8);
         if (tc && (kw & 1)) {
@@ -260,6 +308,7 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
     P->tc_tiles = P->tc_tiles128 = 0;
     for (int i = 0; i < count; i++) {
         const BatchChoice& c = P->choice[i];
+        if (c.strassen) continue;
         if (c.path == BMM_PATH_POPC) {
             const int tm_n = (int)ceil_div(P->m[i], POPC_TILE), tn_n = (int)ceil_div(P->n[i], POPC_TILE);
             const double cost = c.nks * M.pc_stage + M.pc_tile;
@@ -356,6 +405,8 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
     P->est_ms = (makespan + pc_makespan) * 1e-6;
 
     // one device allocation: workspace, then the tables
+    const uint64_t off_sws = round256(ws);
+    ws = off_sws + round256(strassen_ws);
     const uint64_t off_probs = round256(ws);
     const uint64_t off_items = round256(off_probs + sizeof(TcProblem) * (uint64_t)count);
     const uint64_t off_ptr = round256(off_items + sizeof(TcWorkItem) * flat.size());
@@ -379,6 +430,7 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
     P->d_pfirst = (int64_t*)(base + off_pfirst);
     P->d_pcjobs = (PopcJob*)(base + off_pcjobs);
     P->d_pctiles = (PopcTile*)(base + off_pctiles);
+    P->strassen_ws = strassen_ws ? (void*)(base + off_sws) : nullptr;
     P->d_ttjobs = (TmaTransposeJob*)(base + off_ttjobs);
     P->d_ttfirst = (int64_t*)(base + off_ttfirst);
 
@@ -394,6 +446,12 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
     for (int i = 0; i < count; i++) {
         const int64_t kw = P->k[i] / 64;
         const bool tc = P->choice[i].path != BMM_PATH_POPC;
+        std::memset(&probs[i], 0, sizeof(TcProblem));
+        std::memset(&pcjobs[i], 0, sizeof(PopcJob));
+        if (P->choice[i].strassen) {
+            P->Bt[i] = nullptr;
+            continue;
+        }
         uint64_t* Bt = (uint64_t*)(base + bt_off[i]);
         P->Bt[i] = Bt;
         const uint64_t* Aop = P->A[i];
@@ -407,7 +465,6 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
             Aop = Apad;
             lda = P->kp[i];
         }
-        std::memset(&probs[i], 0, sizeof(TcProblem));
         if (tc) {
             const int64_t kpad = P->kp[i] * 64;
             if (!tc_make_problem(&probs[i], Aop, lda, Bt, P->kp[i], P->C[i], P->n[i] / 64, P->m[i],
@@ -415,7 +472,6 @@ bmm_status plan_build(bmm_batched_plan_s* P) {
                 return BMM_ERR_CUDA;
             probs[i].nks = (int32_t)P->choice[i].nks;
         }
-        std::memset(&pcjobs[i], 0, sizeof(PopcJob));
         pcjobs[i] = {P->A[i], Bt, P->C[i], kw, P->kp[i], P->n[i] / 64,
                      P->m[i], P->k[i], P->n[i], P->op[i], 0};
         // B^T through the TMA form where its pitches allow, else load/store
@@ -496,7 +552,14 @@ bmm_status plan_run(bmm_batched_plan_s* P, cudaStream_t s) {
                                                     P->pad_total);
         BMM_CUDA_TRY(cudaGetLastError());
     }
-    return plan_run_base(P, s);
+    bmm_status st = plan_run_base(P, s);
+    if (st != BMM_OK) return st;
+    for (int i = 0; i < P->count; i++)
+        if (P->choice[i].strassen) {
+            st = execute_plan(P->choice[i].sp, P->A[i], P->B[i], P->C[i], P->strassen_ws, s);
+            if (st != BMM_OK) return st;
+        }
+    return BMM_OK;
 }
 
 void plan_free(bmm_batched_plan_s* P) {
@@ -816,7 +879,17 @@ bmm_status bmm_batched_plan_choice(bmm_batched_plan plan, int32_t i, bmm_batched
     const BatchChoice& c = plan->choice[i];
     std::memset(out, 0, sizeof(*out));
     out->path = c.path;
-    out->strassen_depth = 0;
+    out->strassen_depth = c.strassen ? c.sp.depth : 0;
+    if (c.strassen) {
+        // its own product: the base case's tile over the leaves
+        const bool pair = c.path == BMM_PATH_TC_FP4_PAIR || c.path == BMM_PATH_TC_FP8_PAIR;
+        out->tile_m = c.path == BMM_PATH_POPC ? POPC_TILE : pair ? 2 * TC_TILE_M : TC_TILE_M;
+        out->tile_n = out->tail_n = c.path == BMM_PATH_POPC ? POPC_TILE : TC_TILE_N;
+        out->k_step = c.path == BMM_PATH_POPC ? 256 : (int32_t)op_stage_bits(c.path);
+        out->k_steps = ceil_div(c.sp.kp >> c.sp.depth, out->k_step);
+        out->est_us = 0.0;
+        return BMM_OK;
+    }
     if (c.path == BMM_PATH_POPC) {
         out->tile_m = out->tile_n = out->tail_n = POPC_TILE;
         out->k_step = 256;
@@ -845,6 +918,7 @@ bmm_status bmm_batched_plan_stats(bmm_batched_plan plan, bmm_batched_stats* out)
     out->est_ms = plan->est_ms;
     out->model_measured = plan->model.measured ? 1 : 0;
     out->tensor_path = plan->tc_path;
+    out->strassen_problems = plan->strassen_problems;
     return BMM_OK;
 }
 

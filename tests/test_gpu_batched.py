@@ -300,3 +300,76 @@ def test_empty_batch_plan():
     st = bmm.BatchedStats()
     assert L.bmm_batched_plan_stats(h, ctypes.byref(st)) == bmm.OK and st.problems == 0
     assert L.bmm_batched_plan_destroy(h) == bmm.OK
+
+
+def test_batched_strassen_problems():
+    """Binary problems of 16384^3 get the single-product planner's depth
+    (one level: leaves of 8192) and run as their own Strassen products after
+    the batched launches, on the tensor path or, when sent there, the CUDA
+    cores; a Boolean problem of the same size stays cubic. Every product
+    equals the cubic single product bit for bit and the oracle's sampled
+    rows; a second run replayed from a captured graph is exact too."""
+    if not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    bmm.autotune_clear()
+    big = 16384
+    shapes = [(big, big, big, 0), (512, 768, 1024, 0), (big, big, big, 0),
+              (big, 8192, big, 1), (1024, 1024, 1088, 1)]
+    req = [bmm.PATH_AUTO, bmm.PATH_AUTO, bmm.PATH_POPC, bmm.PATH_AUTO, bmm.PATH_AUTO]
+    sh = torch.cuda.current_stream().cuda_stream
+    dev = []
+    for i, (m, k, n, op) in enumerate(shapes):
+        seed = (73 << 16) + i
+        A, B, C = bmm.empty(m, k), bmm.empty(k, n), bmm.empty(m, n)
+        bitgen.fill_device(A, k, seed, 0, p=density(op, k), stream=sh)
+        bitgen.fill_device(B, n, seed, 1, p=density(op, k), stream=sh)
+        C.fill_(-1)
+        dev.append((A, B, C))
+    plan = bmm.BatchedPlan([s[3] for s in shapes], [d[0] for d in dev], [d[1] for d in dev],
+                           [d[2] for d in dev], [s[0] for s in shapes], [s[1] for s in shapes],
+                           [s[2] for s in shapes], paths=req)
+    want_depth = [1, 0, 1, 0, 0]
+    for i, d in enumerate(want_depth):
+        c = plan.choice(i)
+        assert c["strassen_depth"] == d, (i, c)
+    assert plan.choice(2)["path"] == bmm.PATH_POPC
+    assert plan.choice(0)["path"] in bmm.TENSOR_PATHS
+    st = plan.stats()
+    assert st["strassen_problems"] == 2
+    assert st["tensor_problems"] + st["popc_problems"] == len(shapes)
+    plan.run()
+    bmm.stream_status()
+    rng = np.random.default_rng(73)
+
+    def check():
+        for i, (m, k, n, op) in enumerate(shapes):
+            seed = (73 << 16) + i
+            got = from_dev(dev[i][2], m, n)
+            ref = bmm.empty(m, n)
+            bmm.product(op, dev[i][0], dev[i][1], ref, m, k, n, path=bmm.PATH_TC_FP4_PAIR,
+                        depth=0)
+            bmm.stream_status()
+            assert (got == from_dev(ref, m, n)).all(), f"problem {i} vs cubic"
+            del ref
+            p = density(op, k)
+            B = bitgen.fill_cpu(k, n, seed, 1, p=p)
+            o = O.GF2 if op == bmm.GF2 else O.BOOL
+            for r in sorted(rng.choice(m, 2, replace=False).tolist()):
+                Ar = bitgen.fill_cpu(m, k, seed, 0, p=p, row0=r, nrows=1)
+                assert (got[r] == O.rows(o, Ar, B, k, n)[0]).all(), f"problem {i} row {r}"
+
+    check()
+    for d in dev:
+        d[2].fill_(-1)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        plan.run(stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    bmm.stream_status()
+    check()
+    plan.destroy()
+    del g, dev
+    torch.cuda.empty_cache()

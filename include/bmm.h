@@ -244,7 +244,8 @@ typedef struct {
     int32_t k_step;         /* bits of k per step the tiles run in (k is padded to whole steps) */
     int64_t k_steps;        /* steps of k per tile */
     int32_t strassen_depth; /* 0: cubic in the batched launches; > 0: its own
-                               Strassen product (tile fields: its leaves') */
+                               Strassen product (tile fields: its leaves';
+                               est_us 0: the model covers the batched launches) */
     double est_us;          /* the model's time for all its tiles on one unit (CTA pair or CTA) */
 } bmm_batched_choice;
 bmm_status bmm_batched_plan_choice(bmm_batched_plan plan, int32_t i, bmm_batched_choice *out);

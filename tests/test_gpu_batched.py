@@ -313,9 +313,12 @@ def test_batched_strassen_problems():
         pytest.skip("tensor-core paths need sm_103")
     bmm.autotune_clear()
     big = 16384
+    # the last binary problem's k (16512) pads to 16640 on the tensor path
+    # (leaf k a multiple of 128 bits), so its plan holds a padded copy of A
     shapes = [(big, big, big, 0), (512, 768, 1024, 0), (big, big, big, 0),
-              (big, 8192, big, 1), (1024, 1024, 1088, 1)]
-    req = [bmm.PATH_AUTO, bmm.PATH_AUTO, bmm.PATH_POPC, bmm.PATH_AUTO, bmm.PATH_AUTO]
+              (big, 8192, big, 1), (1024, 1024, 1088, 1), (big + 128, big + 128, big, 0)]
+    req = [bmm.PATH_AUTO, bmm.PATH_AUTO, bmm.PATH_POPC, bmm.PATH_AUTO, bmm.PATH_AUTO,
+           bmm.PATH_AUTO]
     sh = torch.cuda.current_stream().cuda_stream
     dev = []
     for i, (m, k, n, op) in enumerate(shapes):
@@ -328,14 +331,14 @@ def test_batched_strassen_problems():
     plan = bmm.BatchedPlan([s[3] for s in shapes], [d[0] for d in dev], [d[1] for d in dev],
                            [d[2] for d in dev], [s[0] for s in shapes], [s[1] for s in shapes],
                            [s[2] for s in shapes], paths=req)
-    want_depth = [1, 0, 1, 0, 0]
+    want_depth = [1, 0, 1, 0, 0, 1]
     for i, d in enumerate(want_depth):
         c = plan.choice(i)
         assert c["strassen_depth"] == d, (i, c)
     assert plan.choice(2)["path"] == bmm.PATH_POPC
     assert plan.choice(0)["path"] in bmm.TENSOR_PATHS
     st = plan.stats()
-    assert st["strassen_problems"] == 2
+    assert st["strassen_problems"] == 3
     assert st["tensor_problems"] + st["popc_problems"] == len(shapes)
     plan.run()
     bmm.stream_status()

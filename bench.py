@@ -106,6 +106,25 @@ def tensor_pipe(achieved: float, clocks: dict, fallback_mhz: float, fp4: bool = 
                                 f"{mhz} MHz (median under load)"}
 
 
+def strassen_bound(pl: dict, m: int, n: int, product_ms: float, peak: float,
+                   hbm_gbs: float, pipe_peak: float = None) -> dict:
+    """The Strassen path's bound for one binary product: its leaves' work at
+    the base case's peak (TFLOP/s, or Tbop/s on the CUDA cores: 2 per MAC
+    either way) plus its streaming passes' bytes (transpose, padding, every
+    XOR pass) at the measured HBM bandwidth, against the measured product."""
+    d = pl["strassen_depth"]
+    work = 2 * pl["leaves"] * (m >> d) * (pl["kp"] >> d) * (n >> d)
+    base_ms = work / (peak * 1e12) * 1e3
+    pass_ms = pl["pass_bytes"] / (hbm_gbs * 1e9) * 1e3
+    out = {"leaf_work": work, "pass_bytes": pl["pass_bytes"], "peak": peak, "hbm_gbs": hbm_gbs,
+           "bound_ms": base_ms + pass_ms, "base_bound_ms": base_ms, "pass_bound_ms": pass_ms,
+           "product_ms": product_ms, "frac": (base_ms + pass_ms) / product_ms}
+    if pipe_peak:
+        pb = work / (pipe_peak * 1e12) * 1e3 + pass_ms
+        out.update({"pipe_bound_ms": pb, "pipe_frac": pb / product_ms})
+    return out
+
+
 def tensor_peak(pk: dict, pk_kind: str, fp4: bool):
     """Measured bf16 peak scaled to the operand type by the nominal ratio."""
     ratio, kind = (FP4_PER_BF16, "fp4") if fp4 else (FP8_PER_BF16, "fp8")
@@ -596,6 +615,9 @@ def main():
                                    "transpose": tr_ms / args.steps},
             "phase_launches": {"base": base_n, "xor": xor_n, "transpose": tr_n},
             "e2e_host": e2e_host,
+            "gf2_strassen_bound": (strassen_bound(pg, m, n, per_product["gf2"], roof["peak"],
+                                                  pk["hbm_gbs"], roof.get("pipe_peak"))
+                                   if depth_g > 0 else None),
             "target_2pow19": target,
         }
         print(json.dumps(line), flush=True)
@@ -704,7 +726,7 @@ def target_record(torch, bmm, bitgen, stream, pk, pk_kind, no_tune=False) -> dic
             res[form] = {"product_ms": ms, "bops": 2 * n ** 3 / (ms / 1000.0),
                          "path": pl["path"], "base_case": _path_name(pl["path"]),
                          "strassen_depth": pl["strassen_depth"],
-                         "base_ms": base_ms, "roofline": roof,
+                         "base_ms": base_ms, "roofline": roof, "_plan": pl,
                          "timed": "one product" + (" after one untimed" if warm else "")}
         step = 1 << 28  # words per comparison chunk
         res["paths_agree"] = all(bool(torch.equal(C[i:i + step], Ct[i:i + step]))
@@ -719,6 +741,14 @@ def target_record(torch, bmm, bitgen, stream, pk, pk_kind, no_tune=False) -> dic
         t = forms[name]["tensor"]
         t["roofline"].update(tensor_pipe(t["roofline"]["achieved"], clocks, pk["sm_max_mhz"],
                                          t["path"] == bmm.PATH_TC_FP4_PAIR))
+        for form in ("tensor", "popcount"):
+            f = forms[name][form]
+            if f["strassen_depth"] > 0:
+                f["strassen_bound"] = strassen_bound(
+                    f.pop("_plan"), n, n, f["product_ms"], f["roofline"]["peak"], pk["hbm_gbs"],
+                    f["roofline"].get("pipe_peak"))
+            else:
+                f.pop("_plan")
     out["products"] = forms
     out["clocks"] = clocks
     return out

@@ -120,7 +120,14 @@ bmm_status bmm_workspace_size(int32_t op, int64_t m, int64_t k, int64_t n, const
 
 /* What the planner resolves the options to for these sizes: the base-case
  * path, the Strassen depth and how many of its top levels run depth-first,
- * the variant, the number of base-case leaves (7^depth) and the scratch size. */
+ * the variant, the number of base-case leaves (7^depth) and the scratch size.
+ * kp is the k the base case runs with (the tensor paths pad k with zero
+ * columns of A and zero rows of B so that every leaf's k is a multiple of
+ * 128 bits); pass_bytes the bytes that the plan's streaming passes (the
+ * transpose of B, the padded copy of A, every XOR pass of Secs. 3.8-3.11)
+ * read and write in HBM, the base case not counted: with the leaves' MACs it
+ * gives the Strassen path's bound (MACs at the tensor peak + pass_bytes at
+ * the HBM bandwidth). */
 typedef struct {
     int32_t path;
     int32_t strassen_depth;
@@ -129,6 +136,8 @@ typedef struct {
     int64_t leaves;
     uint64_t workspace_bytes;
     int32_t kernel_level;    /* 1: the innermost of the levels runs inside the base case */
+    int64_t kp;
+    uint64_t pass_bytes;
 } bmm_plan_info;
 bmm_status bmm_plan(int32_t op, int64_t m, int64_t k, int64_t n, const bmm_opts *opts,
                     bmm_plan_info *info);

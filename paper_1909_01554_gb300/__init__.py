@@ -76,7 +76,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("strassen_depth", ctypes.c_int32),
                 ("serial_depth", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("leaves", ctypes.c_int64), ("workspace_bytes", ctypes.c_uint64),
-                ("kernel_level", ctypes.c_int32)]
+                ("kernel_level", ctypes.c_int32), ("kp", ctypes.c_int64),
+                ("pass_bytes", ctypes.c_uint64)]
 
 
 class BatchedChoice(ctypes.Structure):

@@ -200,6 +200,8 @@ bmm_status bmm_plan(int32_t op, int64_t m, int64_t k, int64_t n, const bmm_opts*
     info->leaves = leaves;
     info->workspace_bytes = p.workspace_bytes;
     info->kernel_level = p.kernel_level;
+    info->kp = p.kp;
+    info->pass_bytes = plan_pass_bytes(p);
     return BMM_OK;
 }
 

@@ -227,3 +227,22 @@ def test_batched_plan_arguments_need_no_gpu(built_lib):
     assert L.bmm_batched_model(9, ctypes.byref(bmm.BatchedModel())) == bmm.ERR_INVALID
     assert L.bmm_batched_model(bmm.PATH_TC_I8, ctypes.byref(bmm.BatchedModel())) == \
         bmm.ERR_UNSUPPORTED
+
+
+def test_plan_pass_bytes_closed_form(built_lib):
+    """The plan's streaming bytes against the closed form of a breadth-first
+    plan (Secs. 3.9 and 3.11 with d levels merged): the transpose reads and
+    writes k n / 8; each operand's expansion reads its matrix once and writes
+    (7/4)^d of it; the compression reads the 7^d leaf products, (7/4)^d m n / 8,
+    and writes C once. Cubic plans move only the transpose."""
+    import paper_1909_01554_gb300 as bmm
+
+    for m, k, n in ((4096, 4096, 4096), (2048, 8192, 1024), (1536, 512, 3072)):
+        cubic = bmm.plan(bmm.GF2, m, k, n, path=bmm.PATH_POPC, depth=0)
+        assert cubic["pass_bytes"] == 2 * k * n // 8 and cubic["kp"] == k
+        for d in (1, 2):
+            pl = bmm.plan(bmm.GF2, m, k, n, path=bmm.PATH_POPC, depth=d, serial=0)
+            assert (pl["strassen_depth"], pl["serial_depth"]) == (d, 0)
+            grow = 7 ** d / 4 ** d
+            want = (2 * k * n + m * k * (1 + grow) + k * n * (1 + grow) + m * n * (1 + grow)) / 8
+            assert pl["pass_bytes"] == want, (m, k, n, d)

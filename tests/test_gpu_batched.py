@@ -376,3 +376,36 @@ def test_batched_strassen_problems():
     plan.destroy()
     del g, dev
     torch.cuda.empty_cache()
+
+
+def test_batched_strassen_problem_follows_the_plan_path():
+    """A plan made on the e4m3 SM-pair path (every entry names it) runs its
+    Strassen problem on that path too: depth 1, bit-identical to the cubic
+    e2m1 product."""
+    if not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    bmm.autotune_clear()
+    big = 16384
+    shapes = [(big, big, big, 0), (512, 640, 768, 1)]
+    sh = torch.cuda.current_stream().cuda_stream
+    dev = []
+    for i, (m, k, n, op) in enumerate(shapes):
+        A, B, C = bmm.empty(m, k), bmm.empty(k, n), bmm.empty(m, n)
+        bitgen.fill_device(A, k, (79 << 16) + i, 0, p=density(op, k), stream=sh)
+        bitgen.fill_device(B, n, (79 << 16) + i, 1, p=density(op, k), stream=sh)
+        C.fill_(-1)
+        dev.append((A, B, C))
+    plan = bmm.BatchedPlan([s[3] for s in shapes], [d[0] for d in dev], [d[1] for d in dev],
+                           [d[2] for d in dev], [s[0] for s in shapes], [s[1] for s in shapes],
+                           [s[2] for s in shapes], path=bmm.PATH_TC_FP8_PAIR)
+    c = plan.choice(0)
+    assert (c["path"], c["strassen_depth"], c["k_step"]) == (bmm.PATH_TC_FP8_PAIR, 1, 128)
+    assert plan.choice(1)["strassen_depth"] == 0
+    plan.run()
+    bmm.stream_status()
+    for i, (m, k, n, op) in enumerate(shapes):
+        ref = bmm.empty(m, n)
+        bmm.product(op, dev[i][0], dev[i][1], ref, m, k, n, path=bmm.PATH_TC_FP4_PAIR, depth=0)
+        bmm.stream_status()
+        assert (from_dev(dev[i][2], m, n) == from_dev(ref, m, n)).all(), f"problem {i}"
+    plan.destroy()

@@ -292,7 +292,8 @@ uint64_t plan_pass_bytes(const Plan& p) {
     const uint64_t la = (uint64_t)(p.m >> d) * (p.kp >> d) / 8;
     const uint64_t lb = (uint64_t)(p.n >> d) * (p.kp >> d) / 8;
     const uint64_t lc = (uint64_t)(p.m >> d) * (p.n >> d) / 8;
-    uint64_t total = 2 * ((uint64_t)p.k * p.n / 8);  // transpose
+    // transpose: B read, Bt written with its padding columns
+    uint64_t total = (uint64_t)p.k * p.n / 8 + (uint64_t)p.kp * p.n / 8;
     if (p.kp != p.k) total += (uint64_t)p.m * p.k / 8 + (uint64_t)p.m * p.kp / 8;  // padded A
     uint64_t reps = 1;                              // executions of the current level
     for (int l = 0; l < p.serial; l++, reps *= 7) {

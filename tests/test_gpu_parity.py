@@ -398,3 +398,20 @@ def test_device_generator_matches_cpu_generator():
         bitgen.fill_device(t, 640, 23, 1, p=p, stream=torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         assert (from_dev(t, 192, 640) == gen(192, 640, 23, 1, p)).all()
+
+
+def test_plan_pass_bytes_with_padded_k():
+    """On the tensor paths a k that is not a multiple of 128 * 2^d bits is
+    padded: the plan's streaming bytes then add the padded copy of A (A read,
+    the copy written) and write Bt at the padded width, and every pass below
+    works on kp (the closed form of a breadth-first plan, Secs. 3.9 and 3.11)."""
+    if not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    m, k, n, d = 2048, 2048 + 256, 1024, 2  # k: a multiple of 64 * 2^d, not of 128 * 2^d
+    pl = bmm.plan(bmm.GF2, m, k, n, path=bmm.PATH_TC_FP4_PAIR, depth=d, serial=0)
+    kp = pl["kp"]
+    assert kp % (128 << d) == 0 and k < kp < k + (128 << d)
+    grow = 7 ** d / 4 ** d
+    want = (k * n + kp * n + m * k + m * kp + m * kp * (1 + grow) + kp * n * (1 + grow)
+            + m * n * (1 + grow)) / 8
+    assert pl["pass_bytes"] == want

@@ -216,7 +216,10 @@ bmm_status bmm_bool_batched(int32_t count, const uint64_t *const *A, const uint6
  * the CUDA cores, one persistent CUDA-core launch, then the Strassen
  * problems one after another; it allocates nothing and
  * does not synchronise, and it reads the matrices named at create time, so new data
- * in the same buffers needs no new plan. destroy frees the plan; call it
+ * in the same buffers needs no new plan. Every run of a plan uses the plan's
+ * own scratch (the transposed B's, padded A's, the Strassen problems'
+ * scratch), so two runs of one plan must not overlap on the GPU (order them
+ * on one stream, or make a plan per stream). destroy frees the plan; call it
  * only after the runs have completed. */
 typedef struct bmm_batched_plan_s *bmm_batched_plan;
 bmm_status bmm_batched_plan_create(int32_t count, const int32_t *op, const uint64_t *const *A,

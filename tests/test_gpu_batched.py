@@ -409,3 +409,37 @@ def test_batched_strassen_problem_follows_the_plan_path():
         bmm.stream_status()
         assert (from_dev(dev[i][2], m, n) == from_dev(ref, m, n)).all(), f"problem {i}"
     plan.destroy()
+
+
+def test_batched_problem_follows_a_tuned_record():
+    """A binary shape the autotuner has recorded gets, inside a batch, the
+    depth (and, with depth > 0, the path) a single product of that shape
+    gets; the product is exact either way."""
+    if not bmm.device_supported():
+        pytest.skip("tensor-core paths need sm_103")
+    n = 8192
+    bmm.autotune_clear()
+    try:
+        bmm.autotune(bmm.GF2, n, n, n)
+        single = bmm.plan(bmm.GF2, n, n, n)
+        shapes = [(n, n, n, 0), (320, 448, 576, 1)]
+        host, dev = make_batch(shapes, 83)
+        plan = bmm.BatchedPlan([s[3] for s in shapes], [d[0] for d in dev],
+                               [d[1] for d in dev], [d[2] for d in dev],
+                               [s[0] for s in shapes], [s[1] for s in shapes],
+                               [s[2] for s in shapes])
+        c = plan.choice(0)
+        assert c["strassen_depth"] == single["strassen_depth"]
+        if single["strassen_depth"] > 0:
+            assert c["path"] == single["path"]
+        plan.run()
+        bmm.stream_status()
+        check_all(shapes, host, dev, which={1})
+        ref = bmm.empty(n, n)
+        bmm.product(bmm.GF2, dev[0][0], dev[0][1], ref, n, n, n, path=bmm.PATH_TC_FP4_PAIR,
+                    depth=0)
+        bmm.stream_status()
+        assert (from_dev(dev[0][2], n, n) == from_dev(ref, n, n)).all()
+        plan.destroy()
+    finally:
+        bmm.autotune_clear()
